@@ -1,0 +1,198 @@
+/*
+ * pmg.h -- C-ABI of the GB300 ILUT-smoothed p-multigrid solver for Galerkin
+ * IgA discretisations of Poisson's equation.
+ *
+ * Method: Tielen, Moeller, Goeddeke, Vuik, "A p-multigrid method enhanced with
+ * an ILUT smoother and its comparison to h-multigrid methods within
+ * Isogeometric Analysis" (arXiv 1901.01685).  The linear system is
+ * A_{h,p} u_{h,p} = f_{h,p} of Sec. 2 (Eq. los); the solver is the V-cycle of
+ * Sec. 3 (two-grid correction scheme applied recursively down to p = 1), with
+ * the ILUT smoother of Sec. 3 "Smoother", the lumped L2-projection transfers
+ * of Sec. 3 "Prolongation and restriction" and an h-multigrid coarse solve at
+ * p = 1; the stopping rule of Sec. 5 (relative residual, divergence above 1e10).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a pmg_status; the library never aborts, traps or
+ *    exits.  On failure pmg_last_error() returns a thread-local message.
+ *  - Vectors are FP64, interior degrees of freedom only (boundary DOFs are
+ *    eliminated, Sec. 5), numbered lexicographically with the first
+ *    parametric direction fastest, 0-based.
+ *  - "_dev" pointers are CUDA device pointers owned by the caller; "_host"
+ *    pointers are host memory owned by the caller.  `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The library allocates no device memory.  The hierarchy is copied into
+ *    a caller-provided device arena (pmg_upload) and each solve uses a
+ *    caller-provided device workspace (pmg_workspace_create).
+ *  - A handle is immutable after pmg_upload and may be shared by concurrent
+ *    solves that use different workspaces.  A workspace serves one solve at
+ *    a time.
+ */
+#ifndef PMG_H_
+#define PMG_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PMG_OK = 0,
+  PMG_ERR_ARG = 1,        /* invalid argument, size or alignment */
+  PMG_ERR_OOM = 2,        /* host allocation failed, or a caller buffer is too small */
+  PMG_ERR_ZERO_PIVOT = 3, /* ILUT met a zero pivot during setup */
+  PMG_ERR_DIVERGED = 4,   /* relative residual above 1e10 (Sec. 5) */
+  PMG_ERR_MAXITER = 5,    /* max_iter V-cycles without reaching rel_tol */
+  PMG_ERR_TIMEOUT = 6,    /* a bounded device-side wait expired; results invalid */
+  PMG_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+  PMG_ERR_BUSY = 8,       /* reserved for admission control */
+  PMG_ERR_STATE = 9       /* call out of order (e.g. solve before upload) */
+} pmg_status;
+
+typedef enum { PMG_QUARTER_ANNULUS = 0, PMG_UNIT_SQUARE = 1, PMG_UNIT_CUBE = 2 } pmg_domain;
+
+/* Manufactured solution used for the load vector and the Dirichlet data.
+ * PMG_U_SINPROD: u = sin(pi x) sin(pi y) [sin(pi z)];
+ * PMG_U_PAPER_B1: benchmark 1 of Sec. 2, u = -(x^2+y^2-1)(x^2+y^2-4) x y^2
+ * (quarter annulus only). */
+typedef enum { PMG_U_SINPROD = 0, PMG_U_PAPER_B1 = 1 } pmg_exact;
+
+/* Residual projection (Sec. 3 and App. A): indirect p -> p-1 -> ... -> 1, or
+ * direct p -> 1. */
+typedef enum { PMG_PROJ_INDIRECT = 0, PMG_PROJ_DIRECT = 1 } pmg_projection;
+
+typedef struct {
+  double drop_tol;    /* ILUT tolerance tau; default 1e-12 (Sec. 3 "Smoother") */
+  double fill_factor; /* ILUT fill factor m; default 1 (Sec. 3 "Smoother") */
+  int nu_pre;         /* pre-smoothing steps nu_1; default 1 (Sec. 5) */
+  int nu_post;        /* post-smoothing steps nu_2; default 1 (Sec. 5) */
+  int projection;     /* pmg_projection; default PMG_PROJ_INDIRECT */
+  int coarse_cycles;  /* h-multigrid V-cycles per coarse solve; default 2 (Sec. 3) */
+  int exact;          /* pmg_exact; default PMG_U_SINPROD */
+  int reserved;       /* must be 0 */
+} pmg_options;
+
+#define PMG_MAX_LEVELS 16
+
+typedef struct {
+  int dim;                              /* 2 or 3 */
+  int p, log2_inv_h;                    /* degree and h = 2^-log2_inv_h */
+  int nlevels;                          /* ILUT-smoothed levels (degrees p .. 2, or p only) */
+  int degree[PMG_MAX_LEVELS];           /* degree of level l (level 0 = p) */
+  int n[PMG_MAX_LEVELS];                /* interior unknowns of level l */
+  long long nnz_A[PMG_MAX_LEVELS];      /* non-zeros of A_l */
+  long long nnz_L[PMG_MAX_LEVELS];      /* non-zeros of the strict lower ILUT factor */
+  long long nnz_U[PMG_MAX_LEVELS];      /* non-zeros of the upper ILUT factor incl. diagonal */
+  long long nnz_P[PMG_MAX_LEVELS];      /* non-zeros of the transfer matrix below level l */
+  int depth_L[PMG_MAX_LEVELS];          /* critical path (wavefronts) of the L solve */
+  int depth_U[PMG_MAX_LEVELS];          /* critical path of the U solve */
+  int nhlevels;                         /* P1 h-multigrid levels incl. the coarsest */
+  int n_h[PMG_MAX_LEVELS];              /* unknowns per P1 level */
+  long long nnz_h[PMG_MAX_LEVELS];      /* non-zeros per P1 operator */
+  int depth_gs[PMG_MAX_LEVELS];         /* critical path of a lexicographic GS sweep */
+  size_t device_bytes;                  /* arena size pmg_upload needs */
+  double setup_ms_assembly, setup_ms_ilut, setup_ms_transfer, setup_ms_hmg;
+  double cycle_bytes;                   /* algorithmic DRAM bytes of one V-cycle */
+  double cycle_flops;                   /* floating-point operations of one V-cycle */
+} pmg_info_t;
+
+typedef struct pmg_hierarchy_s* pmg_handle;
+typedef struct pmg_workspace_s* pmg_ws;
+
+/* Fills `opt` with the paper's settings (tau = 1e-12, m = 1, nu1 = nu2 = 1,
+ * two coarse h-MG cycles) and indirect projection.  PMG_ERR_ARG if opt is NULL. */
+pmg_status pmg_default_options(pmg_options* opt);
+
+/* Builds the hierarchy on the host (Sec. 2 assembly with p+1 Gauss points per
+ * direction, Sec. 3 ILUT factors, lumped L2-projection transfers, p = 1
+ * h-multigrid levels down to h = 2^-3).  No GPU work.  domain: pmg_domain;
+ * p in [2, 8]; log2_inv_h in [3, 12] (<= 6 for the cube).  opt may be NULL
+ * (defaults).  *out receives a handle owned by the caller (pmg_destroy).
+ * Errors: PMG_ERR_ARG, PMG_ERR_OOM, PMG_ERR_ZERO_PIVOT. */
+pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, pmg_handle* out);
+
+/* Sizes, non-zeros, solve depths, setup times and per-cycle algorithmic bytes. */
+pmg_status pmg_info(pmg_handle h, pmg_info_t* info);
+
+/* Copies the hierarchy into `arena_dev` (caller-owned device memory of at least
+ * info.device_bytes bytes, 256-byte aligned) on `stream`, then synchronises the
+ * stream.  The arena must stay valid until pmg_destroy.  Errors: PMG_ERR_ARG
+ * (size or alignment), PMG_ERR_CUDA. */
+pmg_status pmg_upload(pmg_handle h, void* arena_dev, size_t bytes, void* stream);
+
+/* Copies the assembled load vector f (interior, Dirichlet lift applied,
+ * Sec. 2 Eq. los) into f_host (n[0] doubles). */
+pmg_status pmg_rhs(pmg_handle h, double* f_host);
+
+/* Device bytes a workspace for up to max_rhs simultaneous right-hand sides needs. */
+pmg_status pmg_workspace_bytes(pmg_handle h, int max_rhs, size_t* bytes);
+
+/* Creates a workspace in caller-owned device memory `mem_dev` (>= the size from
+ * pmg_workspace_bytes, 256-byte aligned); initialises it on `stream`.
+ * *out is owned by the caller (pmg_ws_destroy). */
+pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem_dev, size_t bytes,
+                                void* stream, pmg_ws* out);
+
+/* Stand-alone p-multigrid solve (Sec. 5): u = u0, then V-cycles until
+ * ||f - A u||_2 / ||f - A u0||_2 < rel_tol, at most max_iter cycles.
+ * f_dev, u0_dev: inputs (n[0] doubles, device).  u_dev: output (device, may
+ * alias u0_dev).  *iters: cycles done.  hist_host[i] (i < min(iters, hist_cap)):
+ * relative residual after cycle i+1.  Blocks until the solve is finished.
+ * Errors: PMG_ERR_DIVERGED, PMG_ERR_MAXITER (iters and history still written),
+ * PMG_ERR_TIMEOUT, PMG_ERR_CUDA, PMG_ERR_STATE. */
+pmg_status pmg_solve(pmg_handle h, pmg_ws ws, const double* f_dev, const double* u0_dev,
+                     double rel_tol, int max_iter, double* u_dev, int* iters,
+                     double* hist_host, int hist_cap, void* stream);
+
+/* As pmg_solve with host buffers: copies f_host and u0_host to the workspace,
+ * solves, copies the solution back to u_host (all on `stream`). */
+pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const double* u0_host,
+                          double rel_tol, int max_iter, double* u_host, int* iters,
+                          double* hist_host, int hist_cap, void* stream);
+
+/* Single steps of the cycle, for checking each one on its own.  `level` is a
+ * p-level index (0 = degree p) for the first group and a P1 level index
+ * (0 = h) for the second.  x, b: inputs; y: output (device).  Sizes follow
+ * the level (coarse side = next level down).
+ *   PMG_OP_RESIDUAL     y = b - A_l x                     (Eq. smooth, Eq. res)
+ *   PMG_OP_SMOOTH       y = x + U^{-1} L^{-1} (b - A_l x) (Eq. inverse)
+ *   PMG_OP_LSOLVE       y = L^{-1} b   (unit lower factor)
+ *   PMG_OP_USOLVE       y = U^{-1} b
+ *   PMG_OP_RESTRICT     y = (M^L_c)^{-1} P^T x  (coarse side)   (Eq. restriction)
+ *   PMG_OP_PROLONG_ADD  y = b + (M^L_l)^{-1} P x (x coarse)     (Eq. prolongation)
+ *   PMG_OP_COARSE_SOLVE y = coarse_cycles h-MG V-cycles on A_{h,1} y = b from 0
+ *   PMG_OP_VCYCLE       y = one V-cycle at level l applied to (x, b)
+ *   PMG_OP_GS_FWD       y = one forward lexicographic Gauss-Seidel sweep (P1 level)
+ *   PMG_OP_GS_BWD       y = one backward sweep
+ *   PMG_OP_HMG_VCYCLE   y = one h-MG V-cycle at P1 level `level` applied to (x, b) */
+enum {
+  PMG_OP_RESIDUAL = 0, PMG_OP_SMOOTH = 1, PMG_OP_LSOLVE = 2, PMG_OP_USOLVE = 3,
+  PMG_OP_RESTRICT = 4, PMG_OP_PROLONG_ADD = 5, PMG_OP_COARSE_SOLVE = 6, PMG_OP_VCYCLE = 7,
+  PMG_OP_GS_FWD = 8, PMG_OP_GS_BWD = 9, PMG_OP_HMG_VCYCLE = 10
+};
+pmg_status pmg_apply(pmg_handle h, pmg_ws ws, int op, int level, const double* x_dev,
+                     const double* b_dev, double* y_dev, void* stream);
+
+/* Host copy of a setup matrix in CSR (for checks).  which: 0 A_l, 1 L_l, 2 U_l
+ * (with diagonal), 3 unscaled P between level l and the next coarser level
+ * (rows: level l), 4 A of P1 level l.  Call with rp == NULL to get sizes. */
+pmg_status pmg_export_csr(pmg_handle h, int which, int level, int* nrows, int* ncols,
+                          long long* nnz, int* rp, int* ci, double* v);
+
+/* Lumped mass (interior) of p-level l, or of V_{h,1} when l == nlevels. */
+pmg_status pmg_export_lumped(pmg_handle h, int level, double* out_host);
+
+/* L2 error against the manufactured solution of the degree-p solution given by
+ * its interior coefficients (host), boundary values from the Dirichlet lift. */
+pmg_status pmg_l2_error(pmg_handle h, const double* u_host, double* err);
+
+pmg_status pmg_ws_destroy(pmg_ws ws);
+pmg_status pmg_destroy(pmg_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMG_H_ */

@@ -1,0 +1,727 @@
+// C-ABI and V-cycle driver of the GB300 p-multigrid solver (see include/pmg.h).
+//
+// The host builds the hierarchy once (setup.cpp); pmg_upload packs it into a
+// caller-owned device arena; every solve step then runs in the CUDA kernels of
+// kernels.cuh on the caller's stream.  The only host<->device traffic per
+// V-cycle is the 8-byte relative residual read for the stopping test.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pmg.h"
+#include "kernels.cuh"
+#include "setup.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pmg_status fail(pmg_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define PMG_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(PMG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kCounterSlots = 256;
+constexpr int kHistCap = 1024;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Layout planner: records (offset, host source, bytes) for every array.
+struct Packer {
+  size_t size = 0;
+  struct Item { size_t off; const void* src; size_t bytes; };
+  std::vector<Item> items;
+  size_t add(const void* src, size_t bytes) {
+    size_t off = size;
+    items.push_back({off, src, bytes});
+    size = align_up(size + std::max<size_t>(bytes, 1));
+    return off;
+  }
+};
+
+struct DevCsrOff { int nr; long long nnz; size_t rp, ci, v; };
+
+DevCsrOff plan_csr(Packer& P, const pmgl::Csr& a) {
+  DevCsrOff o;
+  o.nr = a.nr;
+  o.nnz = a.nnz();
+  o.rp = P.add(a.rp.data(), a.rp.size() * sizeof(int));
+  o.ci = P.add(a.ci.data(), a.ci.size() * sizeof(int));
+  o.v = P.add(a.v.data(), a.v.size() * sizeof(double));
+  return o;
+}
+
+pmgk::Csr bind(const DevCsrOff& o, char* base) {
+  return pmgk::Csr{o.nr, reinterpret_cast<const int*>(base + o.rp), reinterpret_cast<const int*>(base + o.ci),
+                   reinterpret_cast<const double*>(base + o.v)};
+}
+
+struct DevPLevel {
+  int N = 0;
+  double avg_nnz = 0;
+  pmgk::Csr A{}, L{}, U{}, Pro{}, Res{};
+  const double* udinv = nullptr;
+};
+struct DevHLevel {
+  int N = 0, ne = 0;
+  pmgk::Csr A{};
+  const double* dinv = nullptr;
+};
+
+}  // namespace
+
+struct pmg_hierarchy_s {
+  pmgl::Hierarchy H;
+  std::vector<double> udinv_host[PMG_MAX_LEVELS];
+  Packer pack;
+  std::vector<DevCsrOff> off_A, off_L, off_U, off_Pro, off_Res, off_HA;
+  std::vector<size_t> off_udinv, off_dinv;
+  size_t off_cinv = 0;
+  bool uploaded = false;
+  char* arena = nullptr;
+  std::vector<DevPLevel> dl;
+  std::vector<DevHLevel> dh;
+  const double* cinv = nullptr;
+  int sms = 0;
+};
+
+struct pmg_workspace_s {
+  pmg_hierarchy_s* h = nullptr;
+  int max_rhs = 1;
+  // per p-level buffers
+  std::vector<double*> f, u, r, y, e;
+  // P1 levels
+  std::vector<double*> hb, hx, hr;
+  unsigned* flags = nullptr;
+  unsigned* counters = nullptr;
+  unsigned* err = nullptr;
+  double* partial = nullptr;
+  double* r0 = nullptr;
+  double* hist = nullptr;
+  double* f_in = nullptr;   // host-path input staging
+  double* u_io = nullptr;
+  unsigned epoch = 0;
+  int next_slot = 0;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+struct WsLayout {
+  size_t total = 0;
+  std::vector<size_t> f, u, r, y, e, hb, hx, hr;
+  size_t flags, counters, err, partial, r0, hist, f_in, u_io;
+};
+
+WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
+  WsLayout W;
+  size_t s = 0;
+  auto take = [&](size_t bytes) { size_t o = s; s = align_up(s + std::max<size_t>(bytes, 1)); return o; };
+  const auto& H = h->H;
+  int maxN = 0;
+  for (const auto& L : H.lev) {
+    const size_t b = size_t(L.N) * sizeof(double) * max_rhs;
+    W.f.push_back(take(b)); W.u.push_back(take(b)); W.r.push_back(take(b));
+    W.y.push_back(take(b)); W.e.push_back(take(b));
+    maxN = std::max(maxN, L.N);
+  }
+  for (const auto& Hl : H.hl) {
+    const size_t b = size_t(Hl.N) * sizeof(double) * max_rhs;
+    W.hb.push_back(take(b)); W.hx.push_back(take(b)); W.hr.push_back(take(b));
+    maxN = std::max(maxN, Hl.N);
+  }
+  W.flags = take(size_t(maxN) * sizeof(unsigned));
+  W.counters = take(kCounterSlots * sizeof(unsigned));
+  W.err = take(sizeof(unsigned));
+  W.partial = take(pmgk::kNormBlocks * sizeof(double));
+  W.r0 = take(sizeof(double));
+  W.hist = take(kHistCap * sizeof(double));
+  W.f_in = take(size_t(H.lev[0].N) * sizeof(double) * max_rhs);
+  W.u_io = take(size_t(H.lev[0].N) * sizeof(double) * max_rhs);
+  W.total = s;
+  return W;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launch helpers
+// ---------------------------------------------------------------------------
+int grid_for(long long work, int threads, int cap) {
+  long long g = (work + threads - 1) / threads;
+  return int(std::max<long long>(1, std::min<long long>(g, cap)));
+}
+
+template <int MODE>
+void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, double* y, cudaStream_t s, int sms) {
+  const int threads = 256;
+  if (avg >= 24) {
+    pmgk::k_spmv<32, MODE><<<grid_for((long long)A.nr * 32, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+  } else if (avg >= 12) {
+    pmgk::k_spmv<16, MODE><<<grid_for((long long)A.nr * 16, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+  } else {
+    pmgk::k_spmv<8, MODE><<<grid_for((long long)A.nr * 8, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+  }
+}
+
+double avg_nnz(const pmgk::Csr&, long long nnz, int nr) { return nr ? double(nnz) / nr : 0.0; }
+
+struct Ctx {
+  pmg_hierarchy_s* h;
+  pmg_ws w;
+  cudaStream_t s;
+};
+
+unsigned* next_counter(Ctx& c) {
+  if (c.w->next_slot >= kCounterSlots) {
+    cudaMemsetAsync(c.w->counters, 0, kCounterSlots * sizeof(unsigned), c.s);
+    c.w->next_slot = 0;
+  }
+  return c.w->counters + c.w->next_slot++;
+}
+unsigned next_epoch(Ctx& c) {
+  if (++c.w->epoch == 0u) {  // wrapped: clear the flags and restart at 1
+    const auto& H = c.h->H;
+    int maxN = 0;
+    for (const auto& L : H.lev) maxN = std::max(maxN, L.N);
+    for (const auto& Hl : H.hl) maxN = std::max(maxN, Hl.N);
+    cudaMemsetAsync(c.w->flags, 0, size_t(maxN) * sizeof(unsigned), c.s);
+    c.w->epoch = 1u;
+  }
+  return c.w->epoch;
+}
+int sync_grid(const Ctx& c) { return c.h->sms * 4; }
+
+void residual(Ctx& c, int l, const double* f, const double* u, double* r) {
+  const DevPLevel& D = c.h->dl[l];
+  spmv<0>(D.A, D.avg_nnz, u, f, r, c.s, c.h->sms);
+}
+
+void lsolve(Ctx& c, int l, const double* b, double* y) {
+  const DevPLevel& D = c.h->dl[l];
+  pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, next_epoch(c), next_counter(c), c.w->err);
+}
+void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
+  const DevPLevel& D = c.h->dl[l];
+  pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, next_epoch(c),
+                                                        next_counter(c), c.w->err);
+}
+
+// u += U^{-1} L^{-1} r   (one ILUT smoothing step given r = f - A u)
+void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
+  lsolve(c, l, r, c.w->y[l]);
+  usolve(c, l, c.w->y[l], c.w->e[l], u);
+}
+
+void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
+  const DevHLevel& D = c.h->dh[j];
+  if (backward)
+    pmgk::k_gauss_seidel<true><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, next_epoch(c),
+                                                               next_counter(c), c.w->err);
+  else
+    pmgk::k_gauss_seidel<false><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, next_epoch(c),
+                                                                next_counter(c), c.w->err);
+}
+
+// one h-multigrid V-cycle on P1 level j: A_j x = b (Sec. 3, Fig. 1)
+void hmg_vcycle(Ctx& c, int j, const double* b, double* x) {
+  const int nh = int(c.h->dh.size());
+  const DevHLevel& D = c.h->dh[j];
+  if (j == nh - 1) {
+    pmgk::k_dense_matvec<<<grid_for((long long)D.N * 32, 256, c.h->sms * 4), 256, 0, c.s>>>(D.N, c.h->cinv, b, x);
+    return;
+  }
+  const DevHLevel& Cc = c.h->dh[j + 1];
+  const int d = c.h->H.d;
+  gs(c, j, false, b, x);
+  spmv<0>(D.A, 9, x, b, c.w->hr[j], c.s, c.h->sms);
+  pmgk::k_p1_restrict<<<grid_for(Cc.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hr[j], c.w->hb[j + 1]);
+  cudaMemsetAsync(c.w->hx[j + 1], 0, size_t(Cc.N) * sizeof(double), c.s);
+  hmg_vcycle(c, j + 1, c.w->hb[j + 1], c.w->hx[j + 1]);
+  pmgk::k_p1_prolong_add<<<grid_for(D.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hx[j + 1], x);
+  gs(c, j, true, b, x);
+}
+
+// coarse grid correction at p = 1: coarse_cycles h-MG V-cycles from zero
+void coarse_solve(Ctx& c, const double* b1, double* x1) {
+  cudaMemsetAsync(x1, 0, size_t(c.h->dh[0].N) * sizeof(double), c.s);
+  for (int k = 0; k < c.h->H.opt.coarse_cycles; ++k) hmg_vcycle(c, 0, b1, x1);
+}
+
+// V-cycle at p-level l on A_l u = f.  r_in, when not null, holds f - A_l u
+// (the last residual of the previous cycle, or f itself for a zero guess).
+void vcycle(Ctx& c, int l, const double* f, double* u, const double* r_in) {
+  const auto& H = c.h->H;
+  const int nlev = int(c.h->dl.size());
+  const DevPLevel& D = c.h->dl[l];
+  double* r = c.w->r[l];
+  for (int m = 0; m < H.opt.nu_pre; ++m) {
+    const double* rr = r_in;
+    if (!rr) { residual(c, l, f, u, r); rr = r; }
+    smooth_from_residual(c, l, rr, u);
+    r_in = nullptr;
+  }
+  residual(c, l, f, u, r);
+  if (l + 1 < nlev) {
+    const int Nc = c.h->dl[l + 1].N;
+    double* fc = c.w->f[l + 1];
+    double* uc = c.w->u[l + 1];
+    spmv<1>(D.Res, 0, r, nullptr, fc, c.s, c.h->sms);
+    cudaMemsetAsync(uc, 0, size_t(Nc) * sizeof(double), c.s);
+    // with a zero initial guess the first residual is the right-hand side itself
+    vcycle(c, l + 1, fc, uc, fc);
+    spmv<2>(D.Pro, 0, uc, u, u, c.s, c.h->sms);
+  } else {
+    double* b1 = c.w->hb[0];
+    double* x1 = c.w->hx[0];
+    spmv<1>(D.Res, 0, r, nullptr, b1, c.s, c.h->sms);
+    coarse_solve(c, b1, x1);
+    spmv<2>(D.Pro, 0, x1, u, u, c.s, c.h->sms);
+  }
+  for (int m = 0; m < H.opt.nu_post; ++m) {
+    residual(c, l, f, u, r);
+    smooth_from_residual(c, l, r, u);
+  }
+}
+
+void sqnorm(Ctx& c, int n, const double* r, int mode, double* out) {
+  pmgk::k_sqnorm_partial<<<pmgk::kNormBlocks, pmgk::kNormThreads, 0, c.s>>>(n, r, c.w->partial);
+  if (mode == 0)
+    pmgk::k_norm_finalize<0><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, nullptr);
+  else
+    pmgk::k_norm_finalize<1><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, out);
+}
+
+pmg_status check_ws(pmg_handle h, pmg_ws ws) {
+  if (!h || !ws) return fail(PMG_ERR_ARG, "null handle or workspace");
+  if (!h->uploaded) return fail(PMG_ERR_STATE, "hierarchy not uploaded");
+  if (ws->h != h) return fail(PMG_ERR_ARG, "workspace belongs to another hierarchy");
+  return PMG_OK;
+}
+
+pmg_status begin_launches(Ctx& c) {
+  c.w->next_slot = 0;
+  PMG_CUDA(cudaMemsetAsync(c.w->counters, 0, kCounterSlots * sizeof(unsigned), c.s));
+  return PMG_OK;
+}
+
+pmg_status finish_launches(Ctx& c) {
+  PMG_CUDA(cudaGetLastError());
+  unsigned err = 0;
+  PMG_CUDA(cudaMemcpyAsync(&err, c.w->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaStreamSynchronize(c.s));
+  if (err) {
+    cudaMemsetAsync(c.w->err, 0, sizeof(unsigned), c.s);
+    return fail(PMG_ERR_TIMEOUT, "a device-side dependency wait expired");
+  }
+  return PMG_OK;
+}
+
+pmg_status solve_impl(pmg_handle h, pmg_ws ws, const double* f, const double* u0, double tol, int max_iter,
+                      double* u, int* iters, double* hist, int hist_cap, cudaStream_t s) {
+  Ctx c{h, ws, s};
+  const int N = h->dl[0].N;
+  if (iters) *iters = 0;
+  if (u != u0) PMG_CUDA(cudaMemcpyAsync(u, u0, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  double* r = ws->r[0];
+  residual(c, 0, f, u, r);
+  sqnorm(c, N, r, 0, nullptr);
+  double r0 = 0.0;
+  PMG_CUDA(cudaMemcpyAsync(&r0, ws->r0, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  if (r0 == 0.0) return PMG_OK;
+  pmg_status st = PMG_ERR_MAXITER;
+  for (int it = 0; it < max_iter; ++it) {
+    pmg_status b = begin_launches(c);
+    if (b != PMG_OK) return b;
+    vcycle(c, 0, f, u, r);
+    residual(c, 0, f, u, r);
+    double* slot = ws->hist + (it % kHistCap);
+    sqnorm(c, N, r, 1, slot);
+    double rel = 0.0;
+    PMG_CUDA(cudaMemcpyAsync(&rel, slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    pmg_status fin = finish_launches(c);
+    if (fin != PMG_OK) { if (iters) *iters = it + 1; return fin; }
+    if (hist && it < hist_cap) hist[it] = rel;
+    if (iters) *iters = it + 1;
+    if (rel < tol) { st = PMG_OK; break; }
+    if (!(rel <= 1e10)) { st = PMG_ERR_DIVERGED; break; }
+  }
+  if (st == PMG_ERR_MAXITER) g_last_error = "maximum number of V-cycles reached";
+  if (st == PMG_ERR_DIVERGED) g_last_error = "relative residual exceeded 1e10";
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+pmg_status pmg_default_options(pmg_options* opt) {
+  if (!opt) return fail(PMG_ERR_ARG, "opt is NULL");
+  opt->drop_tol = 1e-12;
+  opt->fill_factor = 1.0;
+  opt->nu_pre = 1;
+  opt->nu_post = 1;
+  opt->projection = PMG_PROJ_INDIRECT;
+  opt->coarse_cycles = 2;
+  opt->exact = PMG_U_SINPROD;
+  opt->reserved = 0;
+  return PMG_OK;
+}
+
+pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, pmg_handle* out) {
+  if (!out) return fail(PMG_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  pmg_options o;
+  if (opt) o = *opt; else pmg_default_options(&o);
+  if (o.reserved != 0) return fail(PMG_ERR_ARG, "options.reserved must be 0");
+  pmg_hierarchy_s* h = nullptr;
+  try {
+    h = new pmg_hierarchy_s();
+  } catch (...) {
+    return fail(PMG_ERR_OOM, "host allocation failed");
+  }
+  std::string err;
+  pmg_status st = pmgl::build_hierarchy(domain, p, log2_inv_h, o, h->H, err);
+  if (st != PMG_OK) { delete h; return fail(st, err); }
+  if (h->H.lev.size() > PMG_MAX_LEVELS || h->H.hl.size() > PMG_MAX_LEVELS) { delete h; return fail(PMG_ERR_ARG, "too many levels"); }
+  // device layout
+  Packer& P = h->pack;
+  for (size_t l = 0; l < h->H.lev.size(); ++l) {
+    const auto& L = h->H.lev[l];
+    h->off_A.push_back(plan_csr(P, L.A));
+    h->off_L.push_back(plan_csr(P, L.L));
+    h->off_U.push_back(plan_csr(P, L.U));
+    h->off_Pro.push_back(plan_csr(P, L.Pro));
+    h->off_Res.push_back(plan_csr(P, L.Res));
+    auto& ud = h->udinv_host[l];
+    ud.resize(L.udiag.size());
+    for (size_t i = 0; i < ud.size(); ++i) ud[i] = 1.0 / L.udiag[i];
+    h->off_udinv.push_back(P.add(ud.data(), ud.size() * sizeof(double)));
+  }
+  for (const auto& Hl : h->H.hl) {
+    h->off_HA.push_back(plan_csr(P, Hl.A));
+    h->off_dinv.push_back(P.add(Hl.dinv.data(), Hl.dinv.size() * sizeof(double)));
+  }
+  h->off_cinv = P.add(h->H.coarse_inv.data(), h->H.coarse_inv.size() * sizeof(double));
+  *out = h;
+  return PMG_OK;
+}
+
+pmg_status pmg_info(pmg_handle h, pmg_info_t* info) {
+  if (!h || !info) return fail(PMG_ERR_ARG, "null argument");
+  std::memset(info, 0, sizeof(*info));
+  const auto& H = h->H;
+  info->dim = H.d;
+  info->p = H.p;
+  info->log2_inv_h = H.k;
+  info->nlevels = int(H.lev.size());
+  double bytes = 0, flops = 0;
+  const int nu = H.opt.nu_pre + H.opt.nu_post;
+  for (size_t l = 0; l < H.lev.size(); ++l) {
+    const auto& L = H.lev[l];
+    info->degree[l] = L.q;
+    info->n[l] = L.N;
+    info->nnz_A[l] = L.A.nnz();
+    info->nnz_L[l] = L.L.nnz();
+    info->nnz_U[l] = L.U.nnz() + L.N;
+    info->nnz_P[l] = L.Praw.nnz();
+    info->depth_L[l] = L.depthL;
+    info->depth_U[l] = L.depthU;
+    // residual SpMVs: 1 + nu per cycle (the pre-smoothing one is reused), TRSVs: 2 per smoothing step
+    const double nA = double(L.A.nnz()), nL = double(L.L.nnz()), nU = double(L.U.nnz());
+    const double nP = double(L.Praw.nnz()), N = L.N;
+    const double spmvs = 1 + nu;
+    bytes += spmvs * (12 * nA + 4 * (N + 1) + 3 * 8 * N);
+    bytes += nu * (12 * (nL + nU) + 8 * (N + 1) + 8 * N /*udinv*/ + 6 * 8 * N);
+    bytes += 2 * (12 * nP) + 4 * 2 * (N + 1) + 2 * 3 * 8 * N;
+    flops += spmvs * 2 * nA + nu * (2 * (nL + nU) + 2 * N) + 2 * 2 * nP;
+  }
+  info->nhlevels = int(H.hl.size());
+  for (size_t j = 0; j < H.hl.size(); ++j) {
+    const auto& Hl = H.hl[j];
+    info->n_h[j] = Hl.N;
+    info->nnz_h[j] = Hl.A.nnz();
+    info->depth_gs[j] = Hl.depthGS;
+    const double nA = double(Hl.A.nnz()), N = Hl.N;
+    if (j + 1 < H.hl.size()) {
+      // two GS sweeps + one residual + transfers per h-cycle
+      bytes += H.opt.coarse_cycles * (3 * (12 * nA + 4 * (N + 1) + 3 * 8 * N) + 8 * 8 * N);
+      flops += H.opt.coarse_cycles * (3 * 2 * nA + 2 * 9 * N);
+    } else {
+      bytes += H.opt.coarse_cycles * (8.0 * N * N + 16 * N);
+      flops += H.opt.coarse_cycles * 2.0 * N * N;
+    }
+  }
+  info->device_bytes = h->pack.size;
+  info->setup_ms_assembly = H.t_assembly;
+  info->setup_ms_ilut = H.t_ilut;
+  info->setup_ms_transfer = H.t_transfer;
+  info->setup_ms_hmg = H.t_hmg;
+  info->cycle_bytes = bytes;
+  info->cycle_flops = flops;
+  return PMG_OK;
+}
+
+pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
+  if (!h || !arena) return fail(PMG_ERR_ARG, "null argument");
+  if (bytes < h->pack.size) return fail(PMG_ERR_ARG, "arena too small");
+  if (reinterpret_cast<uintptr_t>(arena) % kAlign) return fail(PMG_ERR_ARG, "arena not 256-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<char> staging(h->pack.size, 0);
+  for (const auto& it : h->pack.items)
+    if (it.bytes) std::memcpy(staging.data() + it.off, it.src, it.bytes);
+  PMG_CUDA(cudaMemcpyAsync(arena, staging.data(), h->pack.size, cudaMemcpyHostToDevice, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  int dev = 0;
+  PMG_CUDA(cudaGetDevice(&dev));
+  PMG_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+  char* base = static_cast<char*>(arena);
+  h->arena = base;
+  h->dl.clear();
+  h->dh.clear();
+  for (size_t l = 0; l < h->H.lev.size(); ++l) {
+    DevPLevel D;
+    D.N = h->H.lev[l].N;
+    D.A = bind(h->off_A[l], base);
+    D.avg_nnz = double(h->off_A[l].nnz) / std::max(1, D.N);
+    D.L = bind(h->off_L[l], base);
+    D.U = bind(h->off_U[l], base);
+    D.Pro = bind(h->off_Pro[l], base);
+    D.Res = bind(h->off_Res[l], base);
+    D.udinv = reinterpret_cast<const double*>(base + h->off_udinv[l]);
+    h->dl.push_back(D);
+  }
+  for (size_t j = 0; j < h->H.hl.size(); ++j) {
+    DevHLevel D;
+    D.N = h->H.hl[j].N;
+    D.ne = h->H.hl[j].ne;
+    D.A = bind(h->off_HA[j], base);
+    D.dinv = reinterpret_cast<const double*>(base + h->off_dinv[j]);
+    h->dh.push_back(D);
+  }
+  h->cinv = reinterpret_cast<const double*>(base + h->off_cinv);
+  h->uploaded = true;
+  return PMG_OK;
+}
+
+pmg_status pmg_rhs(pmg_handle h, double* f_host) {
+  if (!h || !f_host) return fail(PMG_ERR_ARG, "null argument");
+  std::memcpy(f_host, h->H.f.data(), h->H.f.size() * sizeof(double));
+  return PMG_OK;
+}
+
+pmg_status pmg_workspace_bytes(pmg_handle h, int max_rhs, size_t* bytes) {
+  if (!h || !bytes || max_rhs < 1) return fail(PMG_ERR_ARG, "invalid argument");
+  *bytes = plan_ws(h, max_rhs).total;
+  return PMG_OK;
+}
+
+pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t bytes, void* stream, pmg_ws* out) {
+  if (!h || !mem || !out || max_rhs < 1) return fail(PMG_ERR_ARG, "invalid argument");
+  *out = nullptr;
+  WsLayout W = plan_ws(h, max_rhs);
+  if (bytes < W.total) return fail(PMG_ERR_ARG, "workspace memory too small");
+  if (reinterpret_cast<uintptr_t>(mem) % kAlign) return fail(PMG_ERR_ARG, "workspace memory not 256-byte aligned");
+  pmg_workspace_s* w = new (std::nothrow) pmg_workspace_s();
+  if (!w) return fail(PMG_ERR_OOM, "host allocation failed");
+  char* base = static_cast<char*>(mem);
+  auto P = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
+  w->h = h;
+  w->max_rhs = max_rhs;
+  for (size_t l = 0; l < W.f.size(); ++l) {
+    w->f.push_back(P(W.f[l])); w->u.push_back(P(W.u[l])); w->r.push_back(P(W.r[l]));
+    w->y.push_back(P(W.y[l])); w->e.push_back(P(W.e[l]));
+  }
+  for (size_t j = 0; j < W.hb.size(); ++j) {
+    w->hb.push_back(P(W.hb[j])); w->hx.push_back(P(W.hx[j])); w->hr.push_back(P(W.hr[j]));
+  }
+  w->flags = reinterpret_cast<unsigned*>(base + W.flags);
+  w->counters = reinterpret_cast<unsigned*>(base + W.counters);
+  w->err = reinterpret_cast<unsigned*>(base + W.err);
+  w->partial = P(W.partial);
+  w->r0 = P(W.r0);
+  w->hist = P(W.hist);
+  w->f_in = P(W.f_in);
+  w->u_io = P(W.u_io);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(mem, 0, W.total, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { delete w; return fail(PMG_ERR_CUDA, std::string("workspace init: ") + cudaGetErrorString(e)); }
+  *out = w;
+  return PMG_OK;
+}
+
+pmg_status pmg_solve(pmg_handle h, pmg_ws ws, const double* f, const double* u0, double tol, int max_iter,
+                     double* u, int* iters, double* hist, int hist_cap, void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  if (!f || !u0 || !u || max_iter < 1 || !(tol > 0)) return fail(PMG_ERR_ARG, "invalid solve argument");
+  return solve_impl(h, ws, f, u0, tol, max_iter, u, iters, hist, hist_cap, static_cast<cudaStream_t>(stream));
+}
+
+pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const double* u0_host, double tol,
+                          int max_iter, double* u_host, int* iters, double* hist, int hist_cap, void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  if (!f_host || !u0_host || !u_host || max_iter < 1 || !(tol > 0)) return fail(PMG_ERR_ARG, "invalid solve argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = size_t(h->dl[0].N) * sizeof(double);
+  PMG_CUDA(cudaMemcpyAsync(ws->f_in, f_host, bytes, cudaMemcpyHostToDevice, s));
+  PMG_CUDA(cudaMemcpyAsync(ws->u_io, u0_host, bytes, cudaMemcpyHostToDevice, s));
+  st = solve_impl(h, ws, ws->f_in, ws->u_io, tol, max_iter, ws->u_io, iters, hist, hist_cap, s);
+  if (st == PMG_ERR_CUDA || st == PMG_ERR_TIMEOUT) return st;
+  std::string keep = g_last_error;
+  PMG_CUDA(cudaMemcpyAsync(u_host, ws->u_io, bytes, cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  g_last_error = keep;
+  return st;
+}
+
+pmg_status pmg_apply(pmg_handle h, pmg_ws ws, int op, int level, const double* x, const double* b, double* y,
+                     void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Ctx c{h, ws, s};
+  const int nlev = int(h->dl.size()), nh = int(h->dh.size());
+  const bool plevel_op = op <= PMG_OP_VCYCLE && op != PMG_OP_COARSE_SOLVE;
+  if (plevel_op && (level < 0 || level >= nlev)) return fail(PMG_ERR_ARG, "level out of range");
+  if (!plevel_op && op != PMG_OP_COARSE_SOLVE && (level < 0 || level >= nh)) return fail(PMG_ERR_ARG, "level out of range");
+  st = begin_launches(c);
+  if (st != PMG_OK) return st;
+  switch (op) {
+    case PMG_OP_RESIDUAL:
+      residual(c, level, b, x, y);
+      break;
+    case PMG_OP_SMOOTH: {
+      const int N = h->dl[level].N;
+      if (y != x) PMG_CUDA(cudaMemcpyAsync(y, x, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      residual(c, level, b, y, ws->r[level]);
+      smooth_from_residual(c, level, ws->r[level], y);
+      break;
+    }
+    case PMG_OP_LSOLVE:
+      lsolve(c, level, b, y);
+      break;
+    case PMG_OP_USOLVE:
+      usolve(c, level, b, y, nullptr);
+      break;
+    case PMG_OP_RESTRICT:
+      spmv<1>(h->dl[level].Res, 0, x, nullptr, y, s, h->sms);
+      break;
+    case PMG_OP_PROLONG_ADD:
+      spmv<2>(h->dl[level].Pro, 0, x, b, y, s, h->sms);
+      break;
+    case PMG_OP_COARSE_SOLVE:
+      coarse_solve(c, b, y);
+      break;
+    case PMG_OP_VCYCLE: {
+      const int N = h->dl[level].N;
+      if (y != x) PMG_CUDA(cudaMemcpyAsync(y, x, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      vcycle(c, level, b, y, nullptr);
+      break;
+    }
+    case PMG_OP_GS_FWD:
+    case PMG_OP_GS_BWD: {
+      const int N = h->dh[level].N;
+      if (y != x) PMG_CUDA(cudaMemcpyAsync(y, x, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      gs(c, level, op == PMG_OP_GS_BWD, b, y);
+      break;
+    }
+    case PMG_OP_HMG_VCYCLE: {
+      const int N = h->dh[level].N;
+      if (y != x) PMG_CUDA(cudaMemcpyAsync(y, x, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      hmg_vcycle(c, level, b, y);
+      break;
+    }
+    default:
+      return fail(PMG_ERR_ARG, "unknown op");
+  }
+  return finish_launches(c);
+}
+
+pmg_status pmg_export_csr(pmg_handle h, int which, int level, int* nr, int* nc, long long* nnz, int* rp, int* ci,
+                          double* v) {
+  if (!h || !nr || !nc || !nnz) return fail(PMG_ERR_ARG, "null argument");
+  const auto& H = h->H;
+  pmgl::Csr tmp;
+  const pmgl::Csr* a = nullptr;
+  if (which >= 0 && which <= 3) {
+    if (level < 0 || level >= int(H.lev.size())) return fail(PMG_ERR_ARG, "level out of range");
+    const auto& L = H.lev[size_t(level)];
+    if (which == 0) a = &L.A;
+    if (which == 1) a = &L.L;
+    if (which == 3) a = &L.Praw;
+    if (which == 2) {
+      // U with its diagonal first in each row
+      tmp.nr = tmp.nc = L.N;
+      tmp.rp.assign(size_t(L.N) + 1, 0);
+      for (int i = 0; i < L.N; ++i) {
+        tmp.ci.push_back(i);
+        tmp.v.push_back(L.udiag[size_t(i)]);
+        for (int t = L.U.rp[i]; t < L.U.rp[i + 1]; ++t) { tmp.ci.push_back(L.U.ci[t]); tmp.v.push_back(L.U.v[t]); }
+        tmp.rp[size_t(i) + 1] = int(tmp.ci.size());
+      }
+      a = &tmp;
+    }
+  } else if (which == 4) {
+    if (level < 0 || level >= int(H.hl.size())) return fail(PMG_ERR_ARG, "level out of range");
+    a = &H.hl[size_t(level)].A;
+  } else {
+    return fail(PMG_ERR_ARG, "unknown matrix");
+  }
+  *nr = a->nr;
+  *nc = a->nc;
+  *nnz = a->nnz();
+  if (rp) {
+    if (!ci || !v) return fail(PMG_ERR_ARG, "null output array");
+    std::memcpy(rp, a->rp.data(), a->rp.size() * sizeof(int));
+    std::memcpy(ci, a->ci.data(), a->ci.size() * sizeof(int));
+    std::memcpy(v, a->v.data(), a->v.size() * sizeof(double));
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_export_lumped(pmg_handle h, int level, double* out) {
+  if (!h || !out) return fail(PMG_ERR_ARG, "null argument");
+  const auto& H = h->H;
+  if (level >= 0 && level < int(H.lev.size())) {
+    std::memcpy(out, H.lev[size_t(level)].ML.data(), H.lev[size_t(level)].ML.size() * sizeof(double));
+    return PMG_OK;
+  }
+  if (level == int(H.lev.size())) {
+    std::memcpy(out, H.ML1.data(), H.ML1.size() * sizeof(double));
+    return PMG_OK;
+  }
+  return fail(PMG_ERR_ARG, "level out of range");
+}
+
+pmg_status pmg_l2_error(pmg_handle h, const double* u_host, double* err) {
+  if (!h || !u_host || !err) return fail(PMG_ERR_ARG, "null argument");
+  *err = pmgl::l2_error(h->H, u_host);
+  return PMG_OK;
+}
+
+pmg_status pmg_ws_destroy(pmg_ws ws) {
+  delete ws;
+  return PMG_OK;
+}
+
+pmg_status pmg_destroy(pmg_handle h) {
+  delete h;
+  return PMG_OK;
+}
+
+const char* pmg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// Host-side construction of the p-multigrid hierarchy (library side).
+//
+// Everything here runs once per hierarchy on the host: IgA assembly with Gauss
+// quadrature (Sec. 2), the dual-threshold ILUT factors (Sec. 3 "Smoother"), the
+// lumped L2-projection transfer operators (Sec. 3 "Prolongation and
+// restriction", Eq. PM) and the rediscretised p = 1 h-multigrid levels
+// (Sec. 3, Fig. 1).  The V-cycle itself runs on the GPU (pmg.cu).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pmg.h"
+
+namespace pmgl {
+
+struct Csr {
+  int nr = 0, nc = 0;
+  std::vector<int> rp, ci;
+  std::vector<double> v;
+  long long nnz() const { return rp.empty() ? 0 : rp.back(); }
+};
+
+// One ILUT-smoothed level of degree q >= 2.
+struct PLevel {
+  int q = 0, n1d = 0, N = 0;
+  Csr A;                        // interior stiffness
+  Csr L;                        // strict lower ILUT factor (unit diagonal implied)
+  Csr U;                        // strict upper ILUT factor (diagonal held in udinv)
+  std::vector<double> udiag;    // diagonal of U
+  std::vector<double> ML;       // lumped mass (interior)
+  Csr Pro;                      // (M^L_q)^{-1} P_{qc}^{q}: prolongation, N_q x N_c
+  Csr Res;                      // (M^L_qc)^{-1} (P_{qc}^{q})^T: restriction, N_c x N_q
+  Csr Praw;                     // P_{qc}^{q} unscaled (exported for checks)
+  int depthL = 0, depthU = 0;   // critical-path length (levels) of the two solves
+};
+
+// One P1 level of the coarse h-multigrid.
+struct HLevel {
+  int ne = 0, n1d = 0, N = 0;
+  Csr A;
+  std::vector<double> dinv;
+  int depthGS = 0;
+};
+
+struct Hierarchy {
+  int dom = 0, d = 2, p = 2, k = 3;
+  pmg_options opt{};
+  std::vector<PLevel> lev;      // lev[0] has degree p
+  std::vector<double> ML1;      // lumped mass of V_{h,1}
+  std::vector<HLevel> hl;       // hl[0]: P1 at h; last: coarsest (direct solve)
+  std::vector<double> coarse_inv;   // dense inverse of the coarsest operator
+  std::vector<double> f;        // interior load with Dirichlet lift
+  std::vector<double> uB;       // full-space boundary coefficients, degree p
+  double t_assembly = 0, t_ilut = 0, t_transfer = 0, t_hmg = 0;
+};
+
+// Builds the hierarchy; returns PMG_OK or an error status with `err` set.
+pmg_status build_hierarchy(int domain, int p, int log2_inv_h, const pmg_options& opt,
+                           Hierarchy& H, std::string& err);
+
+// Longest dependency chain of a strict triangular factor (levels of the
+// wavefront schedule); `lower` selects the direction.
+int critical_path(const Csr& T, bool lower);
+
+// L2 error of the degree-p solution (interior coefficients u) against the
+// exact solution, (p+3)^d Gauss points per element.
+double l2_error(const Hierarchy& H, const double* u);
+
+}  // namespace pmgl

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of the C-ABI in include/pmg.h.
+
+Functions carry the C names and only marshal arguments: torch tensors become
+device pointers, the current torch CUDA stream becomes the cudaStream_t, and
+torch provides the device memory for the hierarchy arena and the workspaces.
+Every step of the solve runs in the CUDA kernels of libpmg.so; there is no
+CPU fallback, and importing this module fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+
+PMG_OK, PMG_ERR_ARG, PMG_ERR_OOM, PMG_ERR_ZERO_PIVOT, PMG_ERR_DIVERGED, PMG_ERR_MAXITER, \
+    PMG_ERR_TIMEOUT, PMG_ERR_CUDA, PMG_ERR_BUSY, PMG_ERR_STATE = range(10)
+STATUS_NAMES = {0: "ok", 1: "arg", 2: "oom", 3: "zero_pivot", 4: "diverged", 5: "maxiter",
+                6: "timeout", 7: "cuda", 8: "busy", 9: "state"}
+PMG_QUARTER_ANNULUS, PMG_UNIT_SQUARE, PMG_UNIT_CUBE = 0, 1, 2
+PMG_U_SINPROD, PMG_U_PAPER_B1 = 0, 1
+PMG_PROJ_INDIRECT, PMG_PROJ_DIRECT = 0, 1
+(PMG_OP_RESIDUAL, PMG_OP_SMOOTH, PMG_OP_LSOLVE, PMG_OP_USOLVE, PMG_OP_RESTRICT, PMG_OP_PROLONG_ADD,
+ PMG_OP_COARSE_SOLVE, PMG_OP_VCYCLE, PMG_OP_GS_FWD, PMG_OP_GS_BWD, PMG_OP_HMG_VCYCLE) = range(11)
+PMG_MAX_LEVELS = 16
+
+# every symbol include/pmg.h declares
+EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
+           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_apply", "pmg_export_csr",
+           "pmg_export_lumped", "pmg_l2_error", "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
+
+
+class pmg_options(C.Structure):
+    _fields_ = [("drop_tol", C.c_double), ("fill_factor", C.c_double), ("nu_pre", C.c_int),
+                ("nu_post", C.c_int), ("projection", C.c_int), ("coarse_cycles", C.c_int),
+                ("exact", C.c_int), ("reserved", C.c_int)]
+
+
+_L16 = C.c_int * PMG_MAX_LEVELS
+_LL16 = C.c_longlong * PMG_MAX_LEVELS
+
+
+class pmg_info_t(C.Structure):
+    _fields_ = [("dim", C.c_int), ("p", C.c_int), ("log2_inv_h", C.c_int), ("nlevels", C.c_int),
+                ("degree", _L16), ("n", _L16), ("nnz_A", _LL16), ("nnz_L", _LL16), ("nnz_U", _LL16),
+                ("nnz_P", _LL16), ("depth_L", _L16), ("depth_U", _L16), ("nhlevels", C.c_int),
+                ("n_h", _L16), ("nnz_h", _LL16), ("depth_gs", _L16), ("device_bytes", C.c_size_t),
+                ("setup_ms_assembly", C.c_double), ("setup_ms_ilut", C.c_double),
+                ("setup_ms_transfer", C.c_double), ("setup_ms_hmg", C.c_double),
+                ("cycle_bytes", C.c_double), ("cycle_flops", C.c_double)]
+
+    def as_dict(self) -> dict:
+        nl, nh = self.nlevels, self.nhlevels
+        d = {k: getattr(self, k) for k in ("dim", "p", "log2_inv_h", "nlevels", "nhlevels", "device_bytes",
+                                          "setup_ms_assembly", "setup_ms_ilut", "setup_ms_transfer",
+                                          "setup_ms_hmg", "cycle_bytes", "cycle_flops")}
+        for k in ("degree", "n", "nnz_A", "nnz_L", "nnz_U", "nnz_P", "depth_L", "depth_U"):
+            d[k] = list(getattr(self, k))[:nl]
+        for k in ("n_h", "nnz_h", "depth_gs"):
+            d[k] = list(getattr(self, k))[:nh]
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Loads libpmg.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libpmg.so missing at {_LIB_PATH}: the CUDA path is required")
+        L = C.CDLL(_LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.pmg_default_options.argtypes = [C.POINTER(pmg_options)]
+        L.pmg_setup.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(pmg_options), C.POINTER(vp)]
+        L.pmg_info.argtypes = [vp, C.POINTER(pmg_info_t)]
+        L.pmg_upload.argtypes = [vp, vp, C.c_size_t, vp]
+        L.pmg_rhs.argtypes = [vp, dp]
+        L.pmg_workspace_bytes.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t)]
+        L.pmg_workspace_create.argtypes = [vp, C.c_int, vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.pmg_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
+        L.pmg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, dp, ip, dp, C.c_int, vp]
+        L.pmg_apply.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
+        L.pmg_export_csr.argtypes = [vp, C.c_int, C.c_int, ip, ip, C.POINTER(C.c_longlong), ip, ip, dp]
+        L.pmg_export_lumped.argtypes = [vp, C.c_int, dp]
+        L.pmg_l2_error.argtypes = [vp, dp, dp]
+        L.pmg_ws_destroy.argtypes = [vp]
+        L.pmg_destroy.argtypes = [vp]
+        L.pmg_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "pmg_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class PmgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().pmg_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(st: int, where: str, allow=()):
+    if st != PMG_OK and st not in allow:
+        raise PmgError(st, where)
+    return st
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C entry points, same names as the C-ABI
+# ---------------------------------------------------------------------------
+def pmg_default_options() -> pmg_options:
+    o = pmg_options()
+    _check(lib().pmg_default_options(C.byref(o)), "pmg_default_options")
+    return o
+
+
+def pmg_setup(domain: int, p: int, log2_inv_h: int, opt: pmg_options | None = None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().pmg_setup(domain, p, log2_inv_h, C.byref(opt) if opt is not None else None, C.byref(h)),
+           "pmg_setup")
+    return h
+
+
+def pmg_info(h) -> pmg_info_t:
+    info = pmg_info_t()
+    _check(lib().pmg_info(h, C.byref(info)), "pmg_info")
+    return info
+
+
+def pmg_upload(h, arena, stream=None):
+    _check(lib().pmg_upload(h, _ptr(arena), arena.numel() * arena.element_size(), _stream(stream)), "pmg_upload")
+
+
+def pmg_rhs(h, n: int) -> np.ndarray:
+    f = np.zeros(n)
+    _check(lib().pmg_rhs(h, _dp(f)), "pmg_rhs")
+    return f
+
+
+def pmg_workspace_bytes(h, max_rhs: int = 1) -> int:
+    b = C.c_size_t()
+    _check(lib().pmg_workspace_bytes(h, max_rhs, C.byref(b)), "pmg_workspace_bytes")
+    return b.value
+
+
+def pmg_workspace_create(h, max_rhs, mem, stream=None) -> C.c_void_p:
+    ws = C.c_void_p()
+    _check(lib().pmg_workspace_create(h, max_rhs, _ptr(mem), mem.numel() * mem.element_size(), _stream(stream),
+                                      C.byref(ws)), "pmg_workspace_create")
+    return ws
+
+
+def pmg_solve(h, ws, f, u0, rel_tol, max_iter, u, hist_cap=256, stream=None, allow=()):
+    iters = C.c_int()
+    hist = np.zeros(hist_cap)
+    st = lib().pmg_solve(h, ws, _ptr(f), _ptr(u0), rel_tol, max_iter, _ptr(u), C.byref(iters), _dp(hist),
+                         hist_cap, _stream(stream))
+    _check(st, "pmg_solve", allow)
+    return iters.value, hist[: min(iters.value, hist_cap)].copy(), st
+
+
+def pmg_solve_host(h, ws, f: np.ndarray, u0: np.ndarray, rel_tol, max_iter, u: np.ndarray, hist_cap=256,
+                   stream=None, allow=()):
+    iters = C.c_int()
+    hist = np.zeros(hist_cap)
+    st = lib().pmg_solve_host(h, ws, _dp(f), _dp(u0), rel_tol, max_iter, _dp(u), C.byref(iters), _dp(hist),
+                              hist_cap, _stream(stream))
+    _check(st, "pmg_solve_host", allow)
+    return iters.value, hist[: min(iters.value, hist_cap)].copy(), st
+
+
+def pmg_apply(h, ws, op, level, x, b, y, stream=None):
+    _check(lib().pmg_apply(h, ws, op, level, _ptr(x), _ptr(b), _ptr(y), _stream(stream)), "pmg_apply")
+
+
+def pmg_export_csr(h, which: int, level: int):
+    nr, nc, nnz = C.c_int(), C.c_int(), C.c_longlong()
+    L = lib()
+    _check(L.pmg_export_csr(h, which, level, C.byref(nr), C.byref(nc), C.byref(nnz), None, None, None),
+           "pmg_export_csr")
+    rp = np.zeros(nr.value + 1, np.int32)
+    ci = np.zeros(nnz.value, np.int32)
+    v = np.zeros(nnz.value)
+    _check(L.pmg_export_csr(h, which, level, C.byref(nr), C.byref(nc), C.byref(nnz), _ip(rp), _ip(ci), _dp(v)),
+           "pmg_export_csr")
+    return nr.value, nc.value, rp, ci, v
+
+
+def pmg_export_lumped(h, level: int, n: int) -> np.ndarray:
+    out = np.zeros(n)
+    _check(lib().pmg_export_lumped(h, level, _dp(out)), "pmg_export_lumped")
+    return out
+
+
+def pmg_l2_error(h, u: np.ndarray) -> float:
+    e = C.c_double()
+    _check(lib().pmg_l2_error(h, _dp(np.ascontiguousarray(u, dtype=np.float64)), C.byref(e)), "pmg_l2_error")
+    return e.value
+
+
+def pmg_ws_destroy(ws):
+    lib().pmg_ws_destroy(ws)
+
+
+def pmg_destroy(h):
+    lib().pmg_destroy(h)
+
+
+def pmg_last_error() -> str:
+    return lib().pmg_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+# Convenience owner: hierarchy + torch-allocated arena + one workspace
+# ---------------------------------------------------------------------------
+class Solver:
+    """Owns a hierarchy, its device arena and one workspace (torch memory)."""
+
+    def __init__(self, domain: int, p: int, log2_inv_h: int, projection: int = PMG_PROJ_INDIRECT,
+                 exact: int = PMG_U_SINPROD, drop_tol: float = 1e-12, fill_factor: float = 1.0,
+                 nu_pre: int = 1, nu_post: int = 1, coarse_cycles: int = 2, device: str = "cuda",
+                 upload: bool = True):
+        opt = pmg_default_options()
+        opt.projection, opt.exact, opt.drop_tol, opt.fill_factor = projection, exact, drop_tol, fill_factor
+        opt.nu_pre, opt.nu_post, opt.coarse_cycles = nu_pre, nu_post, coarse_cycles
+        self.h = pmg_setup(domain, p, log2_inv_h, opt)
+        self.info = pmg_info(self.h).as_dict()
+        self.N = self.info["n"][0]
+        self.arena = self.mem = self.ws = None
+        if upload:
+            self.upload(device)
+
+    def upload(self, device="cuda"):
+        import torch
+        nbytes = max(self.info["device_bytes"], 256)
+        self.arena = torch.empty((nbytes + 255) // 256 * 32, dtype=torch.float64, device=device)
+        pmg_upload(self.h, self.arena)
+        wb = pmg_workspace_bytes(self.h, 1)
+        self.mem = torch.empty((wb + 255) // 256 * 32, dtype=torch.float64, device=device)
+        self.ws = pmg_workspace_create(self.h, 1, self.mem)
+
+    def rhs(self) -> np.ndarray:
+        return pmg_rhs(self.h, self.N)
+
+    def solve(self, f, u0, rel_tol=1e-8, max_iter=100, u=None, allow=()):
+        import torch
+        if u is None:
+            u = torch.empty_like(u0)
+        it, hist, st = pmg_solve(self.h, self.ws, f, u0, rel_tol, max_iter, u, allow=allow)
+        return u, it, hist, st
+
+    def apply(self, op, level, x, b, y):
+        pmg_apply(self.h, self.ws, op, level, x, b, y)
+        return y
+
+    def __del__(self):
+        try:
+            if self.ws is not None:
+                pmg_ws_destroy(self.ws)
+            if getattr(self, "h", None):
+                pmg_destroy(self.h)
+        except Exception:
+            pass
