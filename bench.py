@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 ILUT-smoothed p-multigrid solver.
+
+Metric: MDOF*iterations/s to a relative residual of 1e-8 (interior DOFs x
+V-cycles / solve time, setup excluded, as the paper times solves separately).
+Workload: Poisson on the quarter annulus (polar map), manufactured solution
+sin(pi x) sin(pi y), h = 2^-8, B-spline degrees p = 2, 3, 4, 5, indirect
+projection p -> ... -> 1, ILUT tau = 1e-12, m = 1, nu1 = nu2 = 1, seeded u0 on
+[-1, 1], FP64.  One step = one solve to 1e-8 for each degree.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank solves the same
+independent problems (replicas: the method's triangular solves do not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MDOF*iter/s to 1e-8 relres (plain FP64)"
+UNIT = "MDOF*iter/s"
+DEGREES = (2, 3, 4, 5)
+LOG2H = 8
+WORKLOAD = "quarter annulus Poisson, h=2^-8, p=2..5, indirect p-MG V-cycle, ILUT(1e-12,1), 1e-8 relres"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pmg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1901_01685_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_class: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (otherwise None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = _kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_class and parts[1] == src:
+            return float(parts[2])
+    return None
+
+
+def _oracle_sample(budget_s: float, degrees=(2, 3)):
+    """The FP64 oracle (single host thread) on a bounded sample of the workload."""
+    from oracle import oracle as O
+    from paper_1901_01685_gb300 import inputs
+    hs = [O.Hierarchy(O.ANNULUS, p, LOG2H) for p in degrees]
+    rhs = [h.rhs() for h in hs]
+    u0s = [inputs.initial_guess(h.N[0], 1) for h in hs]
+    units, secs, solves = 0.0, 0.0, 0
+    while secs < budget_s:
+        for h, f, u0 in zip(hs, rhs, u0s):
+            t = time.perf_counter()
+            _, hist, it, st = h.solve(f, u0)
+            secs += time.perf_counter() - t
+            units += h.N[0] * it
+            solves += 1
+    return units / secs / 1e6, secs, solves
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    t_steps = []
+    value_units = 0.0
+    from oracle import oracle as O
+    from paper_1901_01685_gb300 import inputs
+    degrees = (2, 3)
+    hs = [O.Hierarchy(O.ANNULUS, p, LOG2H) for p in degrees]
+    data = [(h.rhs(), inputs.initial_guess(h.N[0], 1)) for h in hs]
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        units = 0.0
+        for h, (f, u0) in zip(hs, data):
+            _, hist, it, st = h.solve(f, u0)
+            units += h.N[0] * it
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            t_steps.append(dt)
+            value_units += units
+    total = sum(t_steps)
+    value = value_units / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "degrees p=2,3 per step", "l2_flush": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "oracle solves of p=2 and p=3 at h=2^-8 per step, setup excluded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1901_01685_gb300 import inputs, pmg
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cases = [(pmg.PMG_QUARTER_ANNULUS, p, LOG2H) for p in DEGREES]
+    workload = WORKLOAD
+    if args.case:
+        dom, p, k = (int(v) for v in args.case.split(","))
+        cases = [(dom, p, k)]
+        workload = f"single case: domain {dom}, p={p}, h=2^-{k}, indirect p-MG, 1e-8 relres"
+    solvers, fdev, u0dev, udev = [], [], [], []
+    for dom, p, k in cases:
+        S = pmg.Solver(dom, p, k)
+        solvers.append(S)
+        fdev.append(torch.as_tensor(S.rhs(), device="cuda"))
+        u0dev.append(torch.as_tensor(inputs.initial_guess(S.N, 1), device="cuda"))
+        udev.append(torch.empty(S.N, dtype=torch.float64, device="cuda"))
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        units = 0
+        iters = []
+        for S, f, u0, u in zip(solvers, fdev, u0dev, udev):
+            _, it, hist, st = S.solve(f, u0, u=u)
+            units += S.N * it
+            iters.append(it)
+        return units, iters
+
+    for _ in range(args.warmup):
+        step()
+    for S in solvers:
+        pmg.pmg_ws_stats(S.ws, reset=True)
+        pmg.pmg_ws_profile(S.ws, True)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    ev_ms, units_total, iters = [], 0, None
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        units, iters = step()
+        e1.record(stream)
+        e1.synchronize()
+        ev_ms.append(e0.elapsed_time(e1))
+        units_total += units
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    stats = [pmg.pmg_ws_stats(S.ws).as_dict() for S in solvers]
+    for S in solvers:
+        pmg.pmg_ws_profile(S.ws, False)
+    t_dev = sum(ev_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev = float(t.item())
+    value = units_total * world / t_dev / 1e6
+
+    # per-kernel-class totals over the timed region
+    classes = {}
+    launches = 0
+    for st in stats:
+        launches += st["total_launches"]
+        for k, v in st["per_class"].items():
+            c = classes.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0})
+            for f in ("ms", "launches", "bytes"):
+                c[f] += v[f]
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    dc = classes[dom]
+    avg_ms = dc["ms"] / max(dc["launches"], 1)
+    bytes_per_launch = dc["bytes"] / max(dc["launches"], 1)
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    total_ms = sum(c["ms"] for c in classes.values())
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    host = []
+    for S, f, u0 in zip(solvers, fdev, u0dev):
+        fh = torch.empty(S.N, dtype=torch.float64, pin_memory=True)
+        uh = torch.empty(S.N, dtype=torch.float64, pin_memory=True)
+        oh = torch.empty(S.N, dtype=torch.float64, pin_memory=True)
+        fh.copy_(f.cpu()); uh.copy_(u0.cpu())
+        host.append((fh.numpy(), uh.numpy(), oh.numpy()))
+    barrier()
+    t0 = time.perf_counter()
+    e2e_units, h2d, d2h = 0, 0, 0
+    for _ in range(args.steps):
+        for S, (fh, uh, oh) in zip(solvers, host):
+            it, hist, st = pmg.pmg_solve_host(S.h, S.ws, fh, uh, 1e-8, 100, oh)
+            e2e_units += S.N * it
+            h2d += 2 * S.N * 8
+            d2h += S.N * 8 + 8 * (it + 1) + 4 * it
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    e2e_value = e2e_units * world / t_e2e / 1e6
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "cases": cases, "dofs": [S.N for S in solvers],
+                   "iterations": iters, "parallelism": f"replicas{world}", "l2_flush": "2x L2 write between steps",
+                   "wall_s": wall},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(dom),
+                     "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
+                     "share_of_kernel_time": dc["ms"] / total_ms if total_ms else None},
+        "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
+                               "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None}
+                           for k, v in classes.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "paper_context": {"hardware": "Intel i7-8650U, serial C++ (G+Smo)",
+                          "MDOF_iter_per_s_h2^-8": {"p2": 1.02, "p3": 0.76, "p4": 0.56, "p5": 0.41},
+                          "note": "paper: benchmark-1 polynomial solution, direct projection"},
+    }
+    if world == 1 and not args.no_cpu_baseline and not args.case:
+        v, secs, solves = _oracle_sample(args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{solves} oracle solves (p=2,3 at h=2^-8, setup excluded), {secs:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

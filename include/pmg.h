@@ -186,6 +186,34 @@ pmg_status pmg_export_lumped(pmg_handle h, int level, double* out_host);
  * its interior coefficients (host), boundary values from the Dirichlet lift. */
 pmg_status pmg_l2_error(pmg_handle h, const double* u_host, double* err);
 
+/* Kernel classes for the per-workspace launch statistics. */
+enum {
+  PMG_K_RESIDUAL = 0,     /* r = f - A u on a p-level */
+  PMG_K_TRANSFER = 1,     /* restriction / prolongation SpMV between p-levels */
+  PMG_K_LSOLVE = 2,       /* forward substitution with the ILUT factor L */
+  PMG_K_USOLVE = 3,       /* backward substitution with U, fused u += e */
+  PMG_K_GS = 4,           /* Gauss-Seidel sweep on a P1 level */
+  PMG_K_P1 = 5,           /* P1 residual and canonical transfers */
+  PMG_K_COARSE = 6,       /* dense coarsest solve */
+  PMG_K_NORM = 7,         /* residual norm and stopping test */
+  PMG_NKERN = 8
+};
+
+typedef struct {
+  double ms[PMG_NKERN];          /* summed CUDA-event time per class (profiling on) */
+  long long launches[PMG_NKERN]; /* launches per class (profiling on) */
+  double bytes[PMG_NKERN];       /* summed algorithmic DRAM bytes per class (profiling on) */
+  long long total_launches;      /* all kernel launches issued through this workspace */
+} pmg_stats_t;
+
+/* Turns per-launch CUDA-event timing on (enable != 0) or off for `ws`.  Events
+ * are recorded on the launch stream around every kernel; their times are
+ * collected when the call that issued them synchronises. */
+pmg_status pmg_ws_profile(pmg_ws ws, int enable);
+
+/* Copies the statistics of `ws` into *out; clears them if reset != 0. */
+pmg_status pmg_ws_stats(pmg_ws ws, pmg_stats_t* out, int reset);
+
 pmg_status pmg_ws_destroy(pmg_ws ws);
 pmg_status pmg_destroy(pmg_handle h);
 

@@ -70,11 +70,13 @@ pmgk::Csr bind(const DevCsrOff& o, char* base) {
 struct DevPLevel {
   int N = 0;
   double avg_nnz = 0;
+  long long nnzA = 0, nnzL = 0, nnzU = 0, nnzP = 0;
   pmgk::Csr A{}, L{}, U{}, Pro{}, Res{};
   const double* udinv = nullptr;
 };
 struct DevHLevel {
   int N = 0, ne = 0;
+  long long nnzA = 0;
   pmgk::Csr A{};
   const double* dinv = nullptr;
 };
@@ -113,7 +115,19 @@ struct pmg_workspace_s {
   double* u_io = nullptr;
   unsigned epoch = 0;
   int next_slot = 0;
-  cudaStream_t stream = nullptr;
+  // launch statistics (per-kernel CUDA-event timing when prof is on)
+  bool prof = false;
+  struct Pending { int cls; cudaEvent_t a, b; double bytes; };
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Pending> pending;
+  double prof_ms[PMG_NKERN] = {0};
+  long long prof_n[PMG_NKERN] = {0};
+  double prof_bytes[PMG_NKERN] = {0};
+  long long launches = 0;
+  ~pmg_workspace_s() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -173,13 +187,51 @@ void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, doub
   }
 }
 
-double avg_nnz(const pmgk::Csr&, long long nnz, int nr) { return nr ? double(nnz) / nr : 0.0; }
-
 struct Ctx {
   pmg_hierarchy_s* h;
   pmg_ws w;
   cudaStream_t s;
 };
+
+cudaEvent_t pool_event(pmg_ws w) {
+  if (w->ev_used == w->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    w->ev_pool.push_back(e);
+  }
+  return w->ev_pool[w->ev_used++];
+}
+
+// Issues one kernel launch (the callable), counting it and, when profiling is
+// on, bracketing it with CUDA events on the launch stream.
+template <class F>
+void launch(Ctx& c, int cls, double bytes, F&& f) {
+  pmg_ws w = c.w;
+  ++w->launches;
+  if (!w->prof) { f(); return; }
+  cudaEvent_t a = pool_event(w), b = pool_event(w);
+  if (!a || !b) { f(); return; }
+  cudaEventRecord(a, c.s);
+  f();
+  cudaEventRecord(b, c.s);
+  w->pending.push_back({cls, a, b, bytes});
+}
+
+// Folds the timings of completed launches into the statistics (stream synced).
+void collect_profile(pmg_ws w) {
+  for (const auto& p : w->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      w->prof_ms[p.cls] += ms;
+      w->prof_n[p.cls] += 1;
+      w->prof_bytes[p.cls] += p.bytes;
+    }
+  }
+  w->pending.clear();
+  w->ev_used = 0;
+}
+
+double csr_bytes(long long nnz, int nr) { return 12.0 * double(nnz) + 4.0 * (nr + 1); }
 
 unsigned* next_counter(Ctx& c) {
   if (c.w->next_slot >= kCounterSlots) {
@@ -203,17 +255,25 @@ int sync_grid(const Ctx& c) { return c.h->sms * 4; }
 
 void residual(Ctx& c, int l, const double* f, const double* u, double* r) {
   const DevPLevel& D = c.h->dl[l];
-  spmv<0>(D.A, D.avg_nnz, u, f, r, c.s, c.h->sms);
+  launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 24.0 * D.N,
+         [&] { spmv<0>(D.A, D.avg_nnz, u, f, r, c.s, c.h->sms); });
 }
 
 void lsolve(Ctx& c, int l, const double* b, double* y) {
   const DevPLevel& D = c.h->dl[l];
-  pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, next_epoch(c), next_counter(c), c.w->err);
+  const unsigned ep = next_epoch(c);
+  unsigned* cnt = next_counter(c);
+  launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
+    pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, ep, cnt, c.w->err);
+  });
 }
 void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
   const DevPLevel& D = c.h->dl[l];
-  pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, next_epoch(c),
-                                                        next_counter(c), c.w->err);
+  const unsigned ep = next_epoch(c);
+  unsigned* cnt = next_counter(c);
+  launch(c, PMG_K_USOLVE, csr_bytes(D.nnzU, D.N) + (u ? 40.0 : 24.0) * D.N, [&] {
+    pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, ep, cnt, c.w->err);
+  });
 }
 
 // u += U^{-1} L^{-1} r   (one ILUT smoothing step given r = f - A u)
@@ -224,12 +284,26 @@ void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
 
 void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   const DevHLevel& D = c.h->dh[j];
-  if (backward)
-    pmgk::k_gauss_seidel<true><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, next_epoch(c),
-                                                               next_counter(c), c.w->err);
-  else
-    pmgk::k_gauss_seidel<false><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, next_epoch(c),
-                                                                next_counter(c), c.w->err);
+  const unsigned ep = next_epoch(c);
+  unsigned* cnt = next_counter(c);
+  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 32.0 * D.N, [&] {
+    if (backward)
+      pmgk::k_gauss_seidel<true><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, ep, cnt, c.w->err);
+    else
+      pmgk::k_gauss_seidel<false><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, ep, cnt, c.w->err);
+  });
+}
+
+// r_c = (M^L_c)^{-1} P^T r and u_out = u_in + (M^L_l)^{-1} P e_c (Eq. restriction / prolongation)
+void restrict_to(Ctx& c, int l, const double* r, double* rc) {
+  const DevPLevel& D = c.h->dl[l];
+  launch(c, PMG_K_TRANSFER, csr_bytes(D.nnzP, D.Res.nr) + 8.0 * (D.N + D.Res.nr),
+         [&] { spmv<1>(D.Res, double(D.nnzP) / std::max(1, D.Res.nr), r, nullptr, rc, c.s, c.h->sms); });
+}
+void prolong_add(Ctx& c, int l, const double* ec, const double* uin, double* uout) {
+  const DevPLevel& D = c.h->dl[l];
+  launch(c, PMG_K_TRANSFER, csr_bytes(D.nnzP, D.N) + 8.0 * (2 * D.N + D.Res.nr),
+         [&] { spmv<2>(D.Pro, double(D.nnzP) / std::max(1, D.N), ec, uin, uout, c.s, c.h->sms); });
 }
 
 // one h-multigrid V-cycle on P1 level j: A_j x = b (Sec. 3, Fig. 1)
@@ -237,17 +311,24 @@ void hmg_vcycle(Ctx& c, int j, const double* b, double* x) {
   const int nh = int(c.h->dh.size());
   const DevHLevel& D = c.h->dh[j];
   if (j == nh - 1) {
-    pmgk::k_dense_matvec<<<grid_for((long long)D.N * 32, 256, c.h->sms * 4), 256, 0, c.s>>>(D.N, c.h->cinv, b, x);
+    launch(c, PMG_K_COARSE, 8.0 * D.N * D.N + 16.0 * D.N, [&] {
+      pmgk::k_dense_matvec<<<grid_for((long long)D.N * 32, 256, c.h->sms * 4), 256, 0, c.s>>>(D.N, c.h->cinv, b, x);
+    });
     return;
   }
   const DevHLevel& Cc = c.h->dh[j + 1];
   const int d = c.h->H.d;
   gs(c, j, false, b, x);
-  spmv<0>(D.A, 9, x, b, c.w->hr[j], c.s, c.h->sms);
-  pmgk::k_p1_restrict<<<grid_for(Cc.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hr[j], c.w->hb[j + 1]);
+  launch(c, PMG_K_P1, csr_bytes(D.nnzA, D.N) + 24.0 * D.N,
+         [&] { spmv<0>(D.A, 9, x, b, c.w->hr[j], c.s, c.h->sms); });
+  launch(c, PMG_K_P1, 8.0 * (D.N + Cc.N), [&] {
+    pmgk::k_p1_restrict<<<grid_for(Cc.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hr[j], c.w->hb[j + 1]);
+  });
   cudaMemsetAsync(c.w->hx[j + 1], 0, size_t(Cc.N) * sizeof(double), c.s);
   hmg_vcycle(c, j + 1, c.w->hb[j + 1], c.w->hx[j + 1]);
-  pmgk::k_p1_prolong_add<<<grid_for(D.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hx[j + 1], x);
+  launch(c, PMG_K_P1, 8.0 * Cc.N + 16.0 * D.N, [&] {
+    pmgk::k_p1_prolong_add<<<grid_for(D.N, 256, c.h->sms * 8), 256, 0, c.s>>>(d, D.ne, c.w->hx[j + 1], x);
+  });
   gs(c, j, true, b, x);
 }
 
@@ -275,17 +356,17 @@ void vcycle(Ctx& c, int l, const double* f, double* u, const double* r_in) {
     const int Nc = c.h->dl[l + 1].N;
     double* fc = c.w->f[l + 1];
     double* uc = c.w->u[l + 1];
-    spmv<1>(D.Res, 0, r, nullptr, fc, c.s, c.h->sms);
+    restrict_to(c, l, r, fc);
     cudaMemsetAsync(uc, 0, size_t(Nc) * sizeof(double), c.s);
     // with a zero initial guess the first residual is the right-hand side itself
     vcycle(c, l + 1, fc, uc, fc);
-    spmv<2>(D.Pro, 0, uc, u, u, c.s, c.h->sms);
+    prolong_add(c, l, uc, u, u);
   } else {
     double* b1 = c.w->hb[0];
     double* x1 = c.w->hx[0];
-    spmv<1>(D.Res, 0, r, nullptr, b1, c.s, c.h->sms);
+    restrict_to(c, l, r, b1);
     coarse_solve(c, b1, x1);
-    spmv<2>(D.Pro, 0, x1, u, u, c.s, c.h->sms);
+    prolong_add(c, l, x1, u, u);
   }
   for (int m = 0; m < H.opt.nu_post; ++m) {
     residual(c, l, f, u, r);
@@ -294,11 +375,15 @@ void vcycle(Ctx& c, int l, const double* f, double* u, const double* r_in) {
 }
 
 void sqnorm(Ctx& c, int n, const double* r, int mode, double* out) {
-  pmgk::k_sqnorm_partial<<<pmgk::kNormBlocks, pmgk::kNormThreads, 0, c.s>>>(n, r, c.w->partial);
-  if (mode == 0)
-    pmgk::k_norm_finalize<0><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, nullptr);
-  else
-    pmgk::k_norm_finalize<1><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, out);
+  launch(c, PMG_K_NORM, 8.0 * n, [&] {
+    pmgk::k_sqnorm_partial<<<pmgk::kNormBlocks, pmgk::kNormThreads, 0, c.s>>>(n, r, c.w->partial);
+  });
+  launch(c, PMG_K_NORM, 8.0 * pmgk::kNormBlocks, [&] {
+    if (mode == 0)
+      pmgk::k_norm_finalize<0><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, nullptr);
+    else
+      pmgk::k_norm_finalize<1><<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->r0, out);
+  });
 }
 
 pmg_status check_ws(pmg_handle h, pmg_ws ws) {
@@ -319,6 +404,7 @@ pmg_status finish_launches(Ctx& c) {
   unsigned err = 0;
   PMG_CUDA(cudaMemcpyAsync(&err, c.w->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
   PMG_CUDA(cudaStreamSynchronize(c.s));
+  collect_profile(c.w);
   if (err) {
     cudaMemsetAsync(c.w->err, 0, sizeof(unsigned), c.s);
     return fail(PMG_ERR_TIMEOUT, "a device-side dependency wait expired");
@@ -338,6 +424,7 @@ pmg_status solve_impl(pmg_handle h, pmg_ws ws, const double* f, const double* u0
   double r0 = 0.0;
   PMG_CUDA(cudaMemcpyAsync(&r0, ws->r0, sizeof(double), cudaMemcpyDeviceToHost, s));
   PMG_CUDA(cudaStreamSynchronize(s));
+  collect_profile(ws);
   if (r0 == 0.0) return PMG_OK;
   pmg_status st = PMG_ERR_MAXITER;
   for (int it = 0; it < max_iter; ++it) {
@@ -499,6 +586,10 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.Pro = bind(h->off_Pro[l], base);
     D.Res = bind(h->off_Res[l], base);
     D.udinv = reinterpret_cast<const double*>(base + h->off_udinv[l]);
+    D.nnzA = h->off_A[l].nnz;
+    D.nnzL = h->off_L[l].nnz;
+    D.nnzU = h->off_U[l].nnz;
+    D.nnzP = h->off_Pro[l].nnz;
     h->dl.push_back(D);
   }
   for (size_t j = 0; j < h->H.hl.size(); ++j) {
@@ -507,6 +598,7 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.ne = h->H.hl[j].ne;
     D.A = bind(h->off_HA[j], base);
     D.dinv = reinterpret_cast<const double*>(base + h->off_dinv[j]);
+    D.nnzA = h->off_HA[j].nnz;
     h->dh.push_back(D);
   }
   h->cinv = reinterpret_cast<const double*>(base + h->off_cinv);
@@ -617,10 +709,10 @@ pmg_status pmg_apply(pmg_handle h, pmg_ws ws, int op, int level, const double* x
       usolve(c, level, b, y, nullptr);
       break;
     case PMG_OP_RESTRICT:
-      spmv<1>(h->dl[level].Res, 0, x, nullptr, y, s, h->sms);
+      restrict_to(c, level, x, y);
       break;
     case PMG_OP_PROLONG_ADD:
-      spmv<2>(h->dl[level].Pro, 0, x, b, y, s, h->sms);
+      prolong_add(c, level, x, b, y);
       break;
     case PMG_OP_COARSE_SOLVE:
       coarse_solve(c, b, y);
@@ -709,6 +801,27 @@ pmg_status pmg_export_lumped(pmg_handle h, int level, double* out) {
 pmg_status pmg_l2_error(pmg_handle h, const double* u_host, double* err) {
   if (!h || !u_host || !err) return fail(PMG_ERR_ARG, "null argument");
   *err = pmgl::l2_error(h->H, u_host);
+  return PMG_OK;
+}
+
+pmg_status pmg_ws_profile(pmg_ws ws, int enable) {
+  if (!ws) return fail(PMG_ERR_ARG, "null workspace");
+  ws->prof = enable != 0;
+  return PMG_OK;
+}
+
+pmg_status pmg_ws_stats(pmg_ws ws, pmg_stats_t* out, int reset) {
+  if (!ws || !out) return fail(PMG_ERR_ARG, "null argument");
+  for (int k = 0; k < PMG_NKERN; ++k) {
+    out->ms[k] = ws->prof_ms[k];
+    out->launches[k] = ws->prof_n[k];
+    out->bytes[k] = ws->prof_bytes[k];
+  }
+  out->total_launches = ws->launches;
+  if (reset) {
+    for (int k = 0; k < PMG_NKERN; ++k) { ws->prof_ms[k] = 0; ws->prof_n[k] = 0; ws->prof_bytes[k] = 0; }
+    ws->launches = 0;
+  }
   return PMG_OK;
 }
 

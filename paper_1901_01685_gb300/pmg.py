@@ -31,7 +31,10 @@ PMG_MAX_LEVELS = 16
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
            "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_apply", "pmg_export_csr",
-           "pmg_export_lumped", "pmg_l2_error", "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
+           "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_ws_destroy",
+           "pmg_destroy", "pmg_last_error")
+PMG_NKERN = 8
+KERNEL_CLASSES = ("residual", "transfer", "lsolve", "usolve", "gauss_seidel", "p1", "coarse", "norm")
 
 
 class pmg_options(C.Structure):
@@ -65,6 +68,16 @@ class pmg_info_t(C.Structure):
         return d
 
 
+class pmg_stats_t(C.Structure):
+    _fields_ = [("ms", C.c_double * PMG_NKERN), ("launches", C.c_longlong * PMG_NKERN),
+                ("bytes", C.c_double * PMG_NKERN), ("total_launches", C.c_longlong)]
+
+    def as_dict(self) -> dict:
+        return {"total_launches": self.total_launches,
+                "per_class": {KERNEL_CLASSES[k]: {"ms": self.ms[k], "launches": self.launches[k],
+                                                   "bytes": self.bytes[k]} for k in range(PMG_NKERN)}}
+
+
 _lib = None
 
 
@@ -91,6 +104,8 @@ def lib():
         L.pmg_export_csr.argtypes = [vp, C.c_int, C.c_int, ip, ip, C.POINTER(C.c_longlong), ip, ip, dp]
         L.pmg_export_lumped.argtypes = [vp, C.c_int, dp]
         L.pmg_l2_error.argtypes = [vp, dp, dp]
+        L.pmg_ws_profile.argtypes = [vp, C.c_int]
+        L.pmg_ws_stats.argtypes = [vp, C.POINTER(pmg_stats_t), C.c_int]
         L.pmg_ws_destroy.argtypes = [vp]
         L.pmg_destroy.argtypes = [vp]
         L.pmg_last_error.restype = C.c_char_p
@@ -229,6 +244,16 @@ def pmg_l2_error(h, u: np.ndarray) -> float:
     e = C.c_double()
     _check(lib().pmg_l2_error(h, _dp(np.ascontiguousarray(u, dtype=np.float64)), C.byref(e)), "pmg_l2_error")
     return e.value
+
+
+def pmg_ws_profile(ws, enable: bool):
+    _check(lib().pmg_ws_profile(ws, int(bool(enable))), "pmg_ws_profile")
+
+
+def pmg_ws_stats(ws, reset: bool = False) -> pmg_stats_t:
+    st = pmg_stats_t()
+    _check(lib().pmg_ws_stats(ws, C.byref(st), int(bool(reset))), "pmg_ws_stats")
+    return st
 
 
 def pmg_ws_destroy(ws):
