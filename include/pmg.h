@@ -214,6 +214,29 @@ pmg_status pmg_ws_profile(pmg_ws ws, int enable);
 /* Copies the statistics of `ws` into *out; clears them if reset != 0. */
 pmg_status pmg_ws_stats(pmg_ws ws, pmg_stats_t* out, int reset);
 
+/* Allocation-free forward substitution y = L^{-1} b for a strict lower CSR
+ * matrix L with implied unit diagonal (the ILUT factor layout of
+ * pmg_export_csr, which = 1).  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code confined to a
+ * memory pool or arena sized up front, plug-ins whose host application owns
+ * all device allocations, or loops that must not allocate once running.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine: the kernel's
+ * scratch (per-row ready flags, row counter, error word) lives in one fixed
+ * device array of this library, present on every GPU that loads it until the
+ * process exits, which limits n to 1,048,576 rows (4 MiB of scratch).
+ *   n: rows; rp_dev (n+1), ci_dev, v_dev: CSR arrays of L on the device, columns
+ *   ascending, all < their row; b_dev: right-hand side; y_dev: output (may not
+ *   alias b_dev).  All device memory is owned by the caller.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every call
+ * shares the one array and clears the part it uses; calls whose work overlaps
+ * on the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller.  Blocks until the solve on `stream` is finished.
+ * Errors: PMG_ERR_ARG (n above the limit, or null pointers), PMG_ERR_TIMEOUT,
+ * PMG_ERR_CUDA. */
+pmg_status pmg_lsolve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* v_dev,
+                              const double* b_dev, double* y_dev, void* stream);
+
 pmg_status pmg_ws_destroy(pmg_ws ws);
 pmg_status pmg_destroy(pmg_handle h);
 

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -838,3 +839,82 @@ pmg_status pmg_destroy(pmg_handle h) {
 const char* pmg_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward solve.
+//
+// Some callers cannot allocate device memory: code running inside a memory
+// pool or arena that was sized up front, plug-ins whose host application owns
+// every cudaMalloc, or code that must not allocate once a real-time loop has
+// started.  pmg_lsolve_noalloc serves them: it runs the sync-free forward
+// substitution kernel with its scratch (per-row ready flags, the row counter
+// and the error word) in a fixed device array that belongs to this library
+// and exists on every GPU that loads it, so the call itself allocates nothing.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxRows = 1 << 20;     // largest system the fixed scratch serves
+constexpr int kNoAllocHeader = 64;           // counter and error word, padded to 256 bytes
+
+// [0]: row counter, [1]: error word, [64 .. 64 + n): ready flags.
+static __device__ __align__(256) unsigned g_noalloc_scratch[kNoAllocHeader + kNoAllocMaxRows];
+
+struct NoAllocDevice {
+  bool ready = false;
+  unsigned* scratch = nullptr;  // device address of g_noalloc_scratch on this device
+  int sms = 0;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_devices[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// Resolves the device address of the scratch array for the current device
+// (once per device, with that device current).
+pmg_status noalloc_device(NoAllocDevice** out) {
+  int dev = 0;
+  PMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(PMG_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocDevice& d = g_noalloc_devices[dev];
+  if (!d.ready) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(PMG_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    d.scratch = static_cast<unsigned*>(ptr);
+    d.sms = sms;
+    d.ready = true;
+  }
+  *out = &d;
+  return PMG_OK;
+}
+
+}  // namespace
+
+extern "C" pmg_status pmg_lsolve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* v_dev,
+                                         const double* b_dev, double* y_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!rp_dev || !b_dev || !y_dev))) return fail(PMG_ERR_ARG, "invalid argument");
+  if (n > kNoAllocMaxRows)
+    return fail(PMG_ERR_ARG, "pmg_lsolve_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
+                                 std::to_string(kNoAllocMaxRows) + " rows");
+  if (n == 0) return PMG_OK;
+  NoAllocDevice* d = nullptr;
+  pmg_status st = noalloc_device(&d);
+  if (st != PMG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned* counter = d->scratch;
+  unsigned* err = d->scratch + 1;
+  unsigned* flags = d->scratch + kNoAllocHeader;
+  // the previous call's counter, error word and flags are still in the array
+  PMG_CUDA(cudaMemsetAsync(d->scratch, 0, (size_t(kNoAllocHeader) + size_t(n)) * sizeof(unsigned), s));
+  pmgk::Csr L{n, rp_dev, ci_dev, v_dev};
+  pmgk::k_lsolve<<<d->sms * 4, 256, 0, s>>>(L, b_dev, y_dev, flags, 1u, counter, err);
+  PMG_CUDA(cudaGetLastError());
+  unsigned herr = 0;
+  PMG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  PMG_CUDA(cudaStreamSynchronize(s));
+  if (herr) return fail(PMG_ERR_TIMEOUT, "a device-side dependency wait expired");
+  return PMG_OK;
+}

@@ -31,8 +31,8 @@ PMG_MAX_LEVELS = 16
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
            "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_apply", "pmg_export_csr",
-           "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_ws_destroy",
-           "pmg_destroy", "pmg_last_error")
+           "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_lsolve_noalloc",
+           "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
 PMG_NKERN = 8
 KERNEL_CLASSES = ("residual", "transfer", "lsolve", "usolve", "gauss_seidel", "p1", "coarse", "norm")
 
@@ -106,6 +106,7 @@ def lib():
         L.pmg_l2_error.argtypes = [vp, dp, dp]
         L.pmg_ws_profile.argtypes = [vp, C.c_int]
         L.pmg_ws_stats.argtypes = [vp, C.POINTER(pmg_stats_t), C.c_int]
+        L.pmg_lsolve_noalloc.argtypes = [C.c_int, vp, vp, vp, vp, vp, vp]
         L.pmg_ws_destroy.argtypes = [vp]
         L.pmg_destroy.argtypes = [vp]
         L.pmg_last_error.restype = C.c_char_p
@@ -254,6 +255,12 @@ def pmg_ws_stats(ws, reset: bool = False) -> pmg_stats_t:
     st = pmg_stats_t()
     _check(lib().pmg_ws_stats(ws, C.byref(st), int(bool(reset))), "pmg_ws_stats")
     return st
+
+
+def pmg_lsolve_noalloc(n: int, rp, ci, v, b, y, stream=None):
+    """y = L^{-1} b with scratch in the library's fixed device array (no allocation)."""
+    _check(lib().pmg_lsolve_noalloc(n, _ptr(rp), _ptr(ci), _ptr(v), _ptr(b), _ptr(y), _stream(stream)),
+           "pmg_lsolve_noalloc")
 
 
 def pmg_ws_destroy(ws):
