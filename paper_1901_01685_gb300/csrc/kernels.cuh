@@ -296,3 +296,247 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_finalize(int nparts, cons
 }
 
 }  // namespace pmgk
+
+namespace pmgk {
+
+// ---------------------------------------------------------------------------
+// Line-pipelined lower-triangular solve
+//   x_i = (b_i - sum_{j<i} M_ij x_j) d_i      (i in the solve's index space;
+//   i' = MIRROR ? n-1-i : i addresses b, x and u, so that an upper factor
+//   stored with mirrored rows and columns is solved by the same kernel).
+//
+// Unknowns are numbered lexicographically, so rows form "lines" of nx
+// consecutive rows.  A row depends on a few earlier rows of its own line and
+// on rows of earlier lines up to a bounded forward offset, so line l can run
+// a bounded number of rows behind line l-1.  Each CTA claims B consecutive
+// lines in order (an atomic counter; lines a CTA waits for belong to running
+// CTAs) and gives each line two warps:
+//  - the producer computes, 8 rows at a time, c_i = (b_i - sum_far M_ij x_j) d_i
+//    over the "far" entries (earlier lines, and own-line entries 32 or more
+//    rows back) from a window-major layout with coalesced loads, after one wait
+//    per window on the rows it needs;
+//  - the chain warp keeps the 32 rows in flight in its lanes and, row by row,
+//    broadcasts the finished x_i and pushes it into the 31 following rows of
+//    the line with one FMA per lane (coefficients stored by column).  Only a
+//    shuffle and one FMA lie on the per-row critical path.
+// Lines of one CTA exchange values and progress through shared memory; other
+// lines through global memory and an epoch-tagged per-line progress word.
+// Every wait is bounded; on expiry the error word is set and the kernel
+// finishes with invalid values instead of hanging.
+// ---------------------------------------------------------------------------
+constexpr int kLpWin = 8;          // rows per producer window (one lane per row)
+constexpr int kLpAhead = 4;        // chain adds c_i this many rows before row i finishes
+constexpr int kLpStage = 16;       // rows of push coefficients per cp.async stage (double buffered)
+constexpr int kLpLinesPerCta = 2;
+constexpr int kLpProducers = 6;    // producer warps per line (windows dealt round-robin)
+
+// "Not yet computed" marker: the all-ones bit pattern, a NaN that floating-point
+// arithmetic never produces (generated NaNs carry the canonical payload).  The
+// solve's output vector is filled with it (byte 0xFF) before the launch; every
+// consumer polls the value itself, so a value and its readiness travel together
+// in one aligned 64-bit access and no fences or counters are needed.
+constexpr unsigned long long kPending = 0xFFFFFFFFFFFFFFFFull;
+
+struct Lp2 {
+  int n, nx, nlines, nwin, lpr;
+  const int* wofs;
+  const int* wcol;
+  const double* wval;
+  const int* waitofs;
+  const int* wait;      // (line distance, rows needed) pairs
+  const double* push;   // [n][32]
+  const double* dscale; // [n]
+};
+
+template <bool MIRROR>
+__device__ __forceinline__ int lp_vec(int i, int n) { return MIRROR ? n - 1 - i : i; }
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copies the push coefficients of rows [r0, r0 + kLpStage) of the line
+// (clamped to the line end) into `dst` (kLpStage x 32 doubles): 16-byte
+// chunks, 8 per lane.
+__device__ __forceinline__ void lp_stage_push(double* dst, const double* push, int row0, int r0, int nx, int lane) {
+#pragma unroll
+  for (int t = 0; t < kLpStage * 16 / 32; ++t) {
+    const int chunk = t * 32 + lane;       // 16 chunks of 16 bytes per row
+    const int r = chunk >> 4, c = (chunk & 15) * 2;
+    if (r0 + r < nx) cp_async16(dst + r * 32 + c, push + (size_t)(row0 + r0 + r) * 32 + c);
+  }
+}
+
+// Bounded poll of a pending value (global memory); producers back off briefly.
+__device__ __forceinline__ double lp_get_global(const double* p, unsigned* err) {
+  unsigned long long v = ld_relaxed_u64(p);
+  if (v != kPending) return __longlong_as_double((long long)v);
+  const long long t0 = clock64();
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(it < 16 ? 32 : 256);
+    v = ld_relaxed_u64(p);
+    if (v != kPending) return __longlong_as_double((long long)v);
+    if ((it & 15u) == 0u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
+      atomicOr(err, 1u);
+      return 0.0;
+    }
+  }
+}
+// Same for a value in shared memory.  BACKOFF: sleep between polls, so that
+// waiting producer warps leave the shared-memory pipe to the chain warp (whose
+// shuffles and shared loads would otherwise queue behind their polls).
+template <bool BACKOFF>
+__device__ __forceinline__ double lp_get_shared(const volatile double* p, unsigned* err) {
+  const volatile unsigned long long* q = reinterpret_cast<const volatile unsigned long long*>(p);
+  unsigned long long v = *q;
+  if (v != kPending) return __longlong_as_double((long long)v);
+  const long long t0 = clock64();
+  for (unsigned it = 1;; ++it) {
+    if (BACKOFF) __nanosleep(it < 16 ? 32 : 256);
+    v = *q;
+    if (v != kPending) return __longlong_as_double((long long)v);
+    if ((it & 31u) == 0u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
+      atomicOr(err, 1u);
+      return 0.0;
+    }
+  }
+}
+
+template <bool MIRROR, bool UPDATE, int LPR>
+__global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
+    k_lp2(Lp2 M, const double* __restrict__ b, double* x, double* u, unsigned* counter, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char lp_smem[];
+  constexpr int B = kLpLinesPerCta, WPL = kLpProducers + 1;
+  __shared__ int s_block;
+  const int nx = M.nx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int myline = warp / WPL, role = warp % WPL;   // role kLpProducers = chain
+  volatile double* xs_all = reinterpret_cast<double*>(lp_smem);   // [B][nx] finished values
+  volatile double* cs_all = xs_all + (size_t)B * nx;              // [B][nx] producer partial sums
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_block = (int)atomicAdd(counter, 1u);
+    for (int t = threadIdx.x; t < 2 * B * nx; t += blockDim.x)
+      reinterpret_cast<volatile unsigned long long*>(xs_all)[t] = kPending;
+    __syncthreads();
+    const int base = s_block * B;
+    if (base >= M.nlines) return;
+    const int cnt = min(B, M.nlines - base);
+    if (myline >= cnt) continue;
+    const int line = base + myline;
+    const int row0 = line * nx;
+    volatile double* xs_line = xs_all + (size_t)myline * nx;
+    volatile double* cs_line = cs_all + (size_t)myline * nx;
+    if (role < kLpProducers) {
+      // ------------------------------ producers ------------------------------
+      // LPR lanes per row.  Cross-lane reductions (shuffles) issued by the
+      // producers measurably slow the chain warp's shuffle/FMA loop, so they
+      // are used only where rows have many far entries (LPR = 4); rows with
+      // few far entries use one lane each (LPR = 1) and no shuffles at all.
+      constexpr int LANES = kLpWin * LPR;
+      for (int w = role; w < M.nwin; w += kLpProducers) {
+        const int W = line * M.nwin + w;
+        const int o = M.wofs[W], K = (M.wofs[W + 1] - o) / LANES;
+        const int ix = w * kLpWin + lane / LPR;
+        double a0 = 0.0, a1 = 0.0;
+        if (lane < LANES && ix < nx) {
+          for (int k0 = 0; k0 < K; k0 += 8) {
+            int jj[8];
+            double vv[8];
+            unsigned long long raw[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const bool in = k0 + t < K;
+              jj[t] = in ? M.wcol[o + LANES * (k0 + t) + lane] : -1;
+              vv[t] = in ? M.wval[o + LANES * (k0 + t) + lane] : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int j = jj[t];
+              raw[t] = 0ull;
+              if (j >= 0) {
+                const int lj = j / nx;
+                raw[t] = lj >= base ? reinterpret_cast<const volatile unsigned long long*>(xs_all)[(size_t)(lj - base) * nx + (j - lj * nx)]
+                                    : ld_relaxed_u64(x + lp_vec<MIRROR>(j, M.n));
+              }
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              double xv = __longlong_as_double((long long)raw[t]);
+              if (raw[t] == kPending) {
+                const int j = jj[t], lj = j / nx;
+                xv = lj >= base ? lp_get_shared<true>(xs_all + (size_t)(lj - base) * nx + (j - lj * nx), err)
+                                : lp_get_global(x + lp_vec<MIRROR>(j, M.n), err);
+              }
+              if (t & 1) a1 = fma(vv[t], xv, a1);
+              else a0 = fma(vv[t], xv, a0);
+            }
+          }
+        }
+        double acc = a0 + a1;
+        if (LPR > 1) {
+#pragma unroll
+          for (int off = 1; off < LPR; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        }
+        if (lane < LANES && (lane % LPR) == 0 && ix < nx) {
+          const int i = row0 + ix;
+          cs_line[ix] = (b[lp_vec<MIRROR>(i, M.n)] - acc) * M.dscale[i];
+        }
+      }
+      if (UPDATE) {
+        // u += x for this line's rows as the chain finishes them
+        for (int ix = role * 32 + lane; ix < nx; ix += 32 * kLpProducers)
+          u[lp_vec<MIRROR>(row0 + ix, M.n)] += lp_get_shared<true>(xs_line + ix, err);
+      }
+      continue;
+    }
+    // -------------------------------- chain --------------------------------
+    double* pbuf = const_cast<double*>(cs_all) + (size_t)B * nx + (size_t)myline * 2 * kLpStage * 32;
+    lp_stage_push(pbuf, M.push, row0, 0, nx, lane);
+    cp_async_commit();
+    double acc = 0.0;
+    if (lane < kLpAhead && lane < nx) acc = lp_get_shared<false>(cs_line + lane, err);
+    for (int ix0 = 0, st = 0; ix0 < nx; ix0 += kLpStage, st ^= 1) {
+      if (ix0 + kLpStage < nx) {
+        lp_stage_push(pbuf + (st ^ 1) * kLpStage * 32, M.push, row0, ix0 + kLpStage, nx, lane);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const volatile double* pc = pbuf + st * kLpStage * 32;
+#pragma unroll
+      for (int q = 0; q < kLpStage; ++q) {
+        const int ix = ix0 + q;
+        if (ix < nx) {
+          const int s = ix & 31;
+          const double coef = pc[q * 32 + ((lane - s - 1) & 31)];
+          const double xi = __shfl_sync(0xffffffffu, acc, s);
+          acc = (lane == s) ? 0.0 : fma(-coef, xi, acc);
+          const int ia = ix + kLpAhead;
+          if (ia < nx && lane == (ia & 31)) acc += lp_get_shared<false>(cs_line + ia, err);
+          if (lane == 0) {
+            xs_line[ix] = xi;
+            x[lp_vec<MIRROR>(row0 + ix, M.n)] = xi;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace pmgk

@@ -68,18 +68,46 @@ pmgk::Csr bind(const DevCsrOff& o, char* base) {
                    reinterpret_cast<const double*>(base + o.v)};
 }
 
+// Arena offsets of one line-pipelined layout.
+struct LpOff { int n, nx, nlines, nwin, lpr; size_t wofs, wcol, wval, waitofs, wait, push, dscale; };
+
+LpOff plan_lp(Packer& P, const pmgl::LpLayout& L) {
+  LpOff o{L.n, L.nx, L.nlines, L.nwin, L.lpr, 0, 0, 0, 0, 0, 0, 0};
+  o.wofs = P.add(L.wofs.data(), L.wofs.size() * sizeof(int));
+  o.wcol = P.add(L.wcol.data(), L.wcol.size() * sizeof(int));
+  o.wval = P.add(L.wval.data(), L.wval.size() * sizeof(double));
+  o.waitofs = P.add(L.waitofs.data(), L.waitofs.size() * sizeof(int));
+  o.wait = P.add(L.wait.data(), L.wait.size() * sizeof(int));
+  o.push = P.add(L.push.data(), L.push.size() * sizeof(double));
+  o.dscale = P.add(L.dscale.data(), L.dscale.size() * sizeof(double));
+  return o;
+}
+
+pmgk::Lp2 bind_lp(const LpOff& o, char* base) {
+  return pmgk::Lp2{o.n, o.nx, o.nlines, o.nwin, o.lpr,
+                   reinterpret_cast<const int*>(base + o.wofs), reinterpret_cast<const int*>(base + o.wcol),
+                   reinterpret_cast<const double*>(base + o.wval), reinterpret_cast<const int*>(base + o.waitofs),
+                   reinterpret_cast<const int*>(base + o.wait), reinterpret_cast<const double*>(base + o.push),
+                   reinterpret_cast<const double*>(base + o.dscale)};
+}
+
+constexpr size_t kLpSmemCap = 200 * 1024;
+
 struct DevPLevel {
   int N = 0;
   double avg_nnz = 0;
   long long nnzA = 0, nnzL = 0, nnzU = 0, nnzP = 0;
   pmgk::Csr A{}, L{}, U{}, Pro{}, Res{};
   const double* udinv = nullptr;
+  pmgk::Lp2 Llp{}, Ulp{};         // line-pipelined layouts (U mirrored)
 };
 struct DevHLevel {
   int N = 0, ne = 0;
   long long nnzA = 0;
-  pmgk::Csr A{};
+  pmgk::Csr A{}, Lo{}, Up{};
   const double* dinv = nullptr;
+  pmgk::Lp2 Lolp{}, UpMlp{};
+  double avg_lo = 0, avg_up = 0;
 };
 
 }  // namespace
@@ -90,6 +118,8 @@ struct pmg_hierarchy_s {
   Packer pack;
   std::vector<DevCsrOff> off_A, off_L, off_U, off_Pro, off_Res, off_HA;
   std::vector<size_t> off_udinv, off_dinv;
+  std::vector<DevCsrOff> off_Lo, off_Up;
+  std::vector<LpOff> off_Llp, off_Ulp, off_Lolp, off_UpMlp;
   size_t off_cinv = 0;
   bool uploaded = false;
   char* arena = nullptr;
@@ -105,8 +135,9 @@ struct pmg_workspace_s {
   // per p-level buffers
   std::vector<double*> f, u, r, y, e;
   // P1 levels
-  std::vector<double*> hb, hx, hr;
+  std::vector<double*> hb, hx, hr, hg;
   unsigned* flags = nullptr;
+  unsigned long long* lprog = nullptr;   // per-line progress words of the line-pipelined solves
   unsigned* counters = nullptr;
   unsigned* err = nullptr;
   double* partial = nullptr;
@@ -135,8 +166,8 @@ namespace {
 
 struct WsLayout {
   size_t total = 0;
-  std::vector<size_t> f, u, r, y, e, hb, hx, hr;
-  size_t flags, counters, err, partial, r0, hist, f_in, u_io;
+  std::vector<size_t> f, u, r, y, e, hb, hx, hr, hg;
+  size_t flags, lprog, counters, err, partial, r0, hist, f_in, u_io;
 };
 
 WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
@@ -153,10 +184,14 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
   }
   for (const auto& Hl : H.hl) {
     const size_t b = size_t(Hl.N) * sizeof(double) * max_rhs;
-    W.hb.push_back(take(b)); W.hx.push_back(take(b)); W.hr.push_back(take(b));
+    W.hb.push_back(take(b)); W.hx.push_back(take(b)); W.hr.push_back(take(b)); W.hg.push_back(take(b));
     maxN = std::max(maxN, Hl.N);
   }
   W.flags = take(size_t(maxN) * sizeof(unsigned));
+  int maxLines = 1;
+  for (const auto& L : H.lev) maxLines = std::max(maxLines, L.N / std::max(1, L.n1d));
+  for (const auto& Hl : H.hl) maxLines = std::max(maxLines, Hl.N / std::max(1, Hl.n1d));
+  W.lprog = take(size_t(maxLines) * sizeof(unsigned long long));
   W.counters = take(kCounterSlots * sizeof(unsigned));
   W.err = take(sizeof(unsigned));
   W.partial = take(pmgk::kNormBlocks * sizeof(double));
@@ -260,19 +295,51 @@ void residual(Ctx& c, int l, const double* f, const double* u, double* r) {
          [&] { spmv<0>(D.A, D.avg_nnz, u, f, r, c.s, c.h->sms); });
 }
 
+// Line-pipelined solve launch (kLpLinesPerCta lines per CTA, two warps per line).
+template <bool MIR, bool UPD, int LPR>
+bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double* u) {
+  const size_t smem = (size_t(2) * pmgk::kLpLinesPerCta * M.nx + size_t(pmgk::kLpLinesPerCta) * 2 * pmgk::kLpStage * 32) *
+                      sizeof(double);
+  if (smem > kLpSmemCap) return false;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(pmgk::k_lp2<MIR, UPD, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLpSmemCap));
+    attr_set = true;
+  }
+  const int nblocks = (M.nlines + pmgk::kLpLinesPerCta - 1) / pmgk::kLpLinesPerCta;
+  const int grid = std::max(1, std::min(nblocks, c.h->sms));
+  unsigned* cnt = next_counter(c);
+  // the output starts as "pending" (all-ones bytes); rows publish by overwriting it
+  cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s);
+  pmgk::k_lp2<MIR, UPD, LPR><<<grid, 32 * (pmgk::kLpProducers + 1) * pmgk::kLpLinesPerCta, smem, c.s>>>(
+      M, b, x, u, cnt, c.w->err);
+  return true;
+}
+
+template <int LPR>
+bool lp_launch_l(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double* x, double* u) {
+  if (mirror) return u ? lp_launch_t<true, true, LPR>(c, M, b, x, u) : lp_launch_t<true, false, LPR>(c, M, b, x, u);
+  return u ? lp_launch_t<false, true, LPR>(c, M, b, x, u) : lp_launch_t<false, false, LPR>(c, M, b, x, u);
+}
+bool lp_launch(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double* x, double* u) {
+  return M.lpr == 4 ? lp_launch_l<4>(c, M, mirror, b, x, u) : lp_launch_l<1>(c, M, mirror, b, x, u);
+}
+
 void lsolve(Ctx& c, int l, const double* b, double* y) {
   const DevPLevel& D = c.h->dl[l];
-  const unsigned ep = next_epoch(c);
-  unsigned* cnt = next_counter(c);
   launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
+    if (lp_launch(c, D.Llp, false, b, y, nullptr)) return;
+    const unsigned ep = next_epoch(c);
+    unsigned* cnt = next_counter(c);
     pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, ep, cnt, c.w->err);
   });
 }
 void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
   const DevPLevel& D = c.h->dl[l];
-  const unsigned ep = next_epoch(c);
-  unsigned* cnt = next_counter(c);
   launch(c, PMG_K_USOLVE, csr_bytes(D.nnzU, D.N) + (u ? 40.0 : 24.0) * D.N, [&] {
+    if (lp_launch(c, D.Ulp, true, y, e, u)) return;
+    const unsigned ep = next_epoch(c);
+    unsigned* cnt = next_counter(c);
     pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, ep, cnt, c.w->err);
   });
 }
@@ -283,11 +350,23 @@ void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
   usolve(c, l, c.w->y[l], c.w->e[l], u);
 }
 
+// One lexicographic Gauss-Seidel sweep as a triangular solve:
+// forward  (D + L) x_new = b - U x_old,  backward  (D + U) x_new = b - L x_old.
+// The new values go to a scratch vector first (the solve polls its output for
+// readiness, so it cannot overwrite x in place) and are copied back.
 void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   const DevHLevel& D = c.h->dh[j];
-  const unsigned ep = next_epoch(c);
-  unsigned* cnt = next_counter(c);
-  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 32.0 * D.N, [&] {
+  double* t = c.w->hr[j];
+  double* xn = c.w->hg[j];
+  const pmgk::Csr& other = backward ? D.Lo : D.Up;
+  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
+    spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms);
+    if (lp_launch(c, backward ? D.UpMlp : D.Lolp, backward, t, xn, nullptr)) {
+      cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+      return;
+    }
+    const unsigned ep = next_epoch(c);
+    unsigned* cnt = next_counter(c);
     if (backward)
       pmgk::k_gauss_seidel<true><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, ep, cnt, c.w->err);
     else
@@ -495,10 +574,16 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     ud.resize(L.udiag.size());
     for (size_t i = 0; i < ud.size(); ++i) ud[i] = 1.0 / L.udiag[i];
     h->off_udinv.push_back(P.add(ud.data(), ud.size() * sizeof(double)));
+    h->off_Llp.push_back(plan_lp(P, L.Llp));
+    h->off_Ulp.push_back(plan_lp(P, L.Ulp));
   }
   for (const auto& Hl : h->H.hl) {
     h->off_HA.push_back(plan_csr(P, Hl.A));
     h->off_dinv.push_back(P.add(Hl.dinv.data(), Hl.dinv.size() * sizeof(double)));
+    h->off_Lo.push_back(plan_csr(P, Hl.Lo));
+    h->off_Up.push_back(plan_csr(P, Hl.Up));
+    h->off_Lolp.push_back(plan_lp(P, Hl.Lolp));
+    h->off_UpMlp.push_back(plan_lp(P, Hl.UpMlp));
   }
   h->off_cinv = P.add(h->H.coarse_inv.data(), h->H.coarse_inv.size() * sizeof(double));
   *out = h;
@@ -591,6 +676,8 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.nnzL = h->off_L[l].nnz;
     D.nnzU = h->off_U[l].nnz;
     D.nnzP = h->off_Pro[l].nnz;
+    D.Llp = bind_lp(h->off_Llp[l], base);
+    D.Ulp = bind_lp(h->off_Ulp[l], base);
     h->dl.push_back(D);
   }
   for (size_t j = 0; j < h->H.hl.size(); ++j) {
@@ -600,6 +687,12 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.A = bind(h->off_HA[j], base);
     D.dinv = reinterpret_cast<const double*>(base + h->off_dinv[j]);
     D.nnzA = h->off_HA[j].nnz;
+    D.Lo = bind(h->off_Lo[j], base);
+    D.Up = bind(h->off_Up[j], base);
+    D.Lolp = bind_lp(h->off_Lolp[j], base);
+    D.UpMlp = bind_lp(h->off_UpMlp[j], base);
+    D.avg_lo = double(h->off_Lo[j].nnz) / std::max(1, D.N);
+    D.avg_up = double(h->off_Up[j].nnz) / std::max(1, D.N);
     h->dh.push_back(D);
   }
   h->cinv = reinterpret_cast<const double*>(base + h->off_cinv);
@@ -637,8 +730,10 @@ pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t byt
   }
   for (size_t j = 0; j < W.hb.size(); ++j) {
     w->hb.push_back(P(W.hb[j])); w->hx.push_back(P(W.hx[j])); w->hr.push_back(P(W.hr[j]));
+    w->hg.push_back(P(W.hg[j]));
   }
   w->flags = reinterpret_cast<unsigned*>(base + W.flags);
+  w->lprog = reinterpret_cast<unsigned long long*>(base + W.lprog);
   w->counters = reinterpret_cast<unsigned*>(base + W.counters);
   w->err = reinterpret_cast<unsigned*>(base + W.err);
   w->partial = P(W.partial);

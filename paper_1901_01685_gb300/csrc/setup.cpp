@@ -666,6 +666,124 @@ bool dense_inverse(int n, std::vector<double> a, std::vector<double>& inv) {
 
 }  // namespace
 
+Csr mirror(const Csr& a) {
+  Csr m;
+  m.nr = a.nr;
+  m.nc = a.nc;
+  m.rp.assign(size_t(a.nr) + 1, 0);
+  m.ci.reserve(a.ci.size());
+  m.v.reserve(a.v.size());
+  for (int r = 0; r < a.nr; ++r) {
+    const int i = a.nr - 1 - r;
+    for (int t = a.rp[i + 1] - 1; t >= a.rp[i]; --t) {
+      m.ci.push_back(a.nc - 1 - a.ci[t]);
+      m.v.push_back(a.v[t]);
+    }
+    m.rp[size_t(r) + 1] = int(m.ci.size());
+  }
+  return m;
+}
+
+std::vector<int> line_split(const Csr& a, int nx) {
+  std::vector<int> sp(size_t(a.nr));
+  for (int i = 0; i < a.nr; ++i) {
+    const int line_start = (i / nx) * nx;
+    int t = a.rp[i];
+    while (t < a.rp[i + 1] && a.ci[t] < line_start) ++t;
+    sp[size_t(i)] = t;
+  }
+  return sp;
+}
+
+Csr strict_part(const Csr& a, bool lower) {
+  Csr s;
+  s.nr = a.nr;
+  s.nc = a.nc;
+  s.rp.assign(size_t(a.nr) + 1, 0);
+  for (int i = 0; i < a.nr; ++i) {
+    for (int t = a.rp[i]; t < a.rp[i + 1]; ++t) {
+      const int j = a.ci[t];
+      if (lower ? j < i : j > i) { s.ci.push_back(j); s.v.push_back(a.v[t]); }
+    }
+    s.rp[size_t(i) + 1] = int(s.ci.size());
+  }
+  return s;
+}
+
+LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lpr) {
+  LpLayout P;
+  P.lpr = lpr;
+  const int lanes = kLpWin * lpr;
+  P.n = M.nr;
+  P.nx = nx;
+  P.nlines = M.nr / nx;
+  P.nwin = (nx + kLpWin - 1) / kLpWin;
+  const int n = M.nr;
+  P.dscale.assign(size_t(n), 1.0);
+  if (dinv) {
+    // the mirrored factors are stored in the solve's index space; dinv is given in it too
+    for (int i = 0; i < n; ++i) P.dscale[size_t(i)] = (*dinv)[size_t(i)];
+  }
+  P.push.assign(size_t(n) * 32, 0.0);
+  const int nwin_total = P.nlines * P.nwin;
+  P.wofs.assign(size_t(nwin_total) + 1, 0);
+  P.waitofs.assign(size_t(nwin_total) + 1, 0);
+  std::vector<std::vector<int>> far(size_t(kLpWin) * lpr);
+  std::vector<std::vector<double>> farv(size_t(kLpWin) * lpr);
+  for (int ln = 0; ln < P.nlines; ++ln) {
+    for (int w = 0; w < P.nwin; ++w) {
+      const int W = ln * P.nwin + w;
+      for (auto& f : far) f.clear();
+      for (auto& f : farv) f.clear();
+      // per referenced line distance: rows needed
+      std::vector<std::pair<int, int>> need;  // (distance, need)
+      auto add_need = [&](int dist, int local) {
+        for (auto& q : need)
+          if (q.first == dist) { q.second = std::max(q.second, local + 1); return; }
+        need.emplace_back(dist, local + 1);
+      };
+      for (int r = 0; r < kLpWin; ++r) {
+        const int ix = w * kLpWin + r;
+        if (ix >= nx) break;
+        const int i = ln * nx + ix;
+        const int line_start = ln * nx;
+        int cnt = 0;
+        for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) {
+          const int j = M.ci[t];
+          const int k = i - j;
+          if (j >= line_start && k <= 31) {
+            P.push[size_t(j) * 32 + (k - 1)] = M.v[t] * P.dscale[size_t(i)];
+            ++P.ring_entries;
+            continue;
+          }
+          const int jl = j / nx;
+          add_need(ln - jl, j - jl * nx);
+          const int lane = lpr * r + (cnt % lpr);
+          far[size_t(lane)].push_back(j);
+          farv[size_t(lane)].push_back(M.v[t]);
+          ++cnt;
+          ++P.far_entries;
+        }
+      }
+      size_t K = 0;
+      for (auto& f : far) K = std::max(K, f.size());
+      P.wofs[size_t(W) + 1] = P.wofs[size_t(W)] + int(lanes * K);
+      for (size_t k = 0; k < K; ++k)
+        for (int l = 0; l < lanes; ++l) {
+          const bool has = k < far[size_t(l)].size();
+          P.wcol.push_back(has ? far[size_t(l)][k] : -1);
+          P.wval.push_back(has ? farv[size_t(l)][k] : 0.0);
+        }
+      std::sort(need.begin(), need.end());
+      for (auto& q : need) { P.wait.push_back(q.first); P.wait.push_back(q.second); }
+      P.waitofs[size_t(W) + 1] = int(P.wait.size() / 2);
+    }
+  }
+  if (P.wcol.empty()) { P.wcol.push_back(-1); P.wval.push_back(0.0); }
+  if (P.wait.empty()) { P.wait.push_back(0); P.wait.push_back(0); }
+  return P;
+}
+
 int critical_path(const Csr& T, bool lower) {
   const int n = T.nr;
   std::vector<int> lvl(size_t(n), 0);
@@ -745,6 +863,15 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
       if (st != PMG_OK) return st;
       L.depthL = critical_path(L.L, true);
       L.depthU = critical_path(L.U, false);
+      L.Lsplit = line_split(L.L, L.n1d);
+      L.Um = mirror(L.U);
+      L.Umsplit = line_split(L.Um, L.n1d);
+      L.Llp = build_lp(L.L, L.n1d, nullptr, 4);
+      {
+        std::vector<double> ud(size_t(L.N));
+        for (int i = 0; i < L.N; ++i) ud[size_t(i)] = 1.0 / L.udiag[size_t(L.N - 1 - i)];
+        L.Ulp = build_lp(L.Um, L.n1d, &ud, 4);
+      }
       H.t_ilut += ms_since(t0);
     }
     auto t0 = clk::now();
@@ -776,6 +903,17 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
         for (int t = Hl.A.rp[i]; t < Hl.A.rp[i + 1]; ++t)
           if (Hl.A.ci[t] == i) Hl.dinv[size_t(i)] = 1.0 / Hl.A.v[t];
       Hl.depthGS = critical_path(Hl.A, true);
+      Hl.Lo = strict_part(Hl.A, true);
+      Hl.Up = strict_part(Hl.A, false);
+      Hl.UpM = mirror(Hl.Up);
+      Hl.Losplit = line_split(Hl.Lo, Hl.n1d);
+      Hl.UpMsplit = line_split(Hl.UpM, Hl.n1d);
+      Hl.Lolp = build_lp(Hl.Lo, Hl.n1d, &Hl.dinv, 1);
+      {
+        std::vector<double> dm(size_t(Hl.N));
+        for (int i = 0; i < Hl.N; ++i) dm[size_t(i)] = Hl.dinv[size_t(Hl.N - 1 - i)];
+        Hl.UpMlp = build_lp(Hl.UpM, Hl.n1d, &dm, 1);
+      }
     }
     {
       const HLevel& C = H.hl.back();

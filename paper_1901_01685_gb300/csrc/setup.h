@@ -21,6 +21,28 @@ struct Csr {
   long long nnz() const { return rp.empty() ? 0 : rp.back(); }
 };
 
+// Device layout of one strict-lower solve  x_i = (b_i - sum_{j<i} M_ij x_j) d_i
+// for the line-pipelined kernel (lines = runs of nx consecutive rows).
+//  - "ring" part: entries in the row's own line at distance 1..31; stored by
+//    column j as push[j*32 + k-1] = M(j+k, j) d_{j+k} (zero if absent or if
+//    j+k lies in another line).
+//  - "far" part: all other entries, grouped in windows of kLpWin rows of one
+//    line with `lpr` lanes per row: lane = lpr*r + s (r: row in window), slot k
+//    of lane l is entry s + lpr*k of that row, wcol/wval[wofs[w] + kLpWin*lpr*k
+//    + l] (col -1 = padding).
+//  - wait list of window w: pairs (line distance, rows needed) in
+//    wait[waitofs[w] .. waitofs[w+1]).
+//  - dscale[i] = d_i (1 when the matrix has a unit diagonal).
+struct LpLayout {
+  int n = 0, nx = 0, nlines = 0, nwin = 0;    // nwin: windows per line
+  int lpr = 1;                                 // lanes per row in the far part
+  std::vector<int> wofs, wcol, waitofs, wait;
+  std::vector<double> wval, push, dscale;
+  long long far_entries = 0, ring_entries = 0;
+};
+constexpr int kLpWin = 8;
+LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lanes_per_row);
+
 // One ILUT-smoothed level of degree q >= 2.
 struct PLevel {
   int q = 0, n1d = 0, N = 0;
@@ -33,6 +55,11 @@ struct PLevel {
   Csr Res;                      // (M^L_qc)^{-1} (P_{qc}^{q})^T: restriction, N_c x N_q
   Csr Praw;                     // P_{qc}^{q} unscaled (exported for checks)
   int depthL = 0, depthU = 0;   // critical-path length (levels) of the two solves
+  // line-pipelined solve layout: lines are runs of n1d consecutive rows
+  std::vector<int> Lsplit;      // per row of L: first entry in the row's own line
+  Csr Um;                       // U with rows and columns mirrored (i -> N-1-i): lower triangular
+  std::vector<int> Umsplit;
+  LpLayout Llp, Ulp;            // line-pipelined layouts of L and mirrored U (with 1/u_ii)
 };
 
 // One P1 level of the coarse h-multigrid.
@@ -41,6 +68,10 @@ struct HLevel {
   Csr A;
   std::vector<double> dinv;
   int depthGS = 0;
+  // Gauss-Seidel as triangular solves: strict lower / upper parts of A
+  Csr Lo, Up, UpM;              // UpM: Up mirrored (lower triangular)
+  std::vector<int> Losplit, UpMsplit;
+  LpLayout Lolp, UpMlp;         // line-pipelined layouts of the two sweeps (with 1/a_ii)
 };
 
 struct Hierarchy {
@@ -58,6 +89,16 @@ struct Hierarchy {
 // Builds the hierarchy; returns PMG_OK or an error status with `err` set.
 pmg_status build_hierarchy(int domain, int p, int log2_inv_h, const pmg_options& opt,
                            Hierarchy& H, std::string& err);
+
+// Mirror of a square matrix: entry (i, j) -> (n-1-i, n-1-j), columns ascending.
+Csr mirror(const Csr& a);
+
+// Per row: index of the first entry whose column lies in the row's own line
+// (lines = runs of nx consecutive rows; columns ascending within each row).
+std::vector<int> line_split(const Csr& a, int nx);
+
+// Strict lower (lower = true) or strict upper part of a square matrix.
+Csr strict_part(const Csr& a, bool lower);
 
 // Longest dependency chain of a strict triangular factor (levels of the
 // wavefront schedule); `lower` selects the direction.
