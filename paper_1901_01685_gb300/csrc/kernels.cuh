@@ -324,7 +324,6 @@ namespace pmgk {
 // Every wait is bounded; on expiry the error word is set and the kernel
 // finishes with invalid values instead of hanging.
 // ---------------------------------------------------------------------------
-constexpr int kLpWin = 8;          // rows per producer window (one lane per row)
 constexpr int kLpAhead = 4;        // chain adds c_i this many rows before row i finishes
 constexpr int kLpStage = 16;       // rows of push coefficients per cp.async stage (double buffered)
 constexpr int kLpLinesPerCta = 2;
@@ -338,7 +337,7 @@ constexpr int kLpProducers = 6;    // producer warps per line (windows dealt rou
 constexpr unsigned long long kPending = 0xFFFFFFFFFFFFFFFFull;
 
 struct Lp2 {
-  int n, nx, nlines, nwin, lpr;
+  int n, nx, nlines, nwin, lpr, win;
   const int* wofs;
   const int* wcol;
   const double* wval;
@@ -414,7 +413,7 @@ __device__ __forceinline__ double lp_get_shared(const volatile double* p, unsign
   }
 }
 
-template <bool MIRROR, bool UPDATE, int LPR>
+template <bool MIRROR, bool UPDATE, int WIN, int LPR>
 __global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
     k_lp2(Lp2 M, const double* __restrict__ b, double* x, double* u, unsigned* counter, unsigned* err) {
   extern __shared__ __align__(16) unsigned char lp_smem[];
@@ -441,15 +440,16 @@ __global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
     volatile double* cs_line = cs_all + (size_t)myline * nx;
     if (role < kLpProducers) {
       // ------------------------------ producers ------------------------------
-      // LPR lanes per row.  Cross-lane reductions (shuffles) issued by the
-      // producers measurably slow the chain warp's shuffle/FMA loop, so they
-      // are used only where rows have many far entries (LPR = 4); rows with
-      // few far entries use one lane each (LPR = 1) and no shuffles at all.
-      constexpr int LANES = kLpWin * LPR;
+      // Windows of WIN rows, LPR lanes per row.  FP64 FMA chains are slow on
+      // this part, so rows with many far entries split them over 8 lanes (short
+      // per-lane chains, small windows); rows with few far entries use one
+      // lane each.
+      static_assert(WIN * LPR <= 32, "window does not fit a warp");
+      constexpr int LANES = WIN * LPR;
       for (int w = role; w < M.nwin; w += kLpProducers) {
         const int W = line * M.nwin + w;
         const int o = M.wofs[W], K = (M.wofs[W + 1] - o) / LANES;
-        const int ix = w * kLpWin + lane / LPR;
+        const int ix = w * WIN + lane / LPR;
         double a0 = 0.0, a1 = 0.0;
         if (lane < LANES && ix < nx) {
           for (int k0 = 0; k0 < K; k0 += 8) {

@@ -69,10 +69,10 @@ pmgk::Csr bind(const DevCsrOff& o, char* base) {
 }
 
 // Arena offsets of one line-pipelined layout.
-struct LpOff { int n, nx, nlines, nwin, lpr; size_t wofs, wcol, wval, waitofs, wait, push, dscale; };
+struct LpOff { int n, nx, nlines, nwin, lpr, win; size_t wofs, wcol, wval, waitofs, wait, push, dscale; };
 
 LpOff plan_lp(Packer& P, const pmgl::LpLayout& L) {
-  LpOff o{L.n, L.nx, L.nlines, L.nwin, L.lpr, 0, 0, 0, 0, 0, 0, 0};
+  LpOff o{L.n, L.nx, L.nlines, L.nwin, L.lpr, L.win, 0, 0, 0, 0, 0, 0, 0};
   o.wofs = P.add(L.wofs.data(), L.wofs.size() * sizeof(int));
   o.wcol = P.add(L.wcol.data(), L.wcol.size() * sizeof(int));
   o.wval = P.add(L.wval.data(), L.wval.size() * sizeof(double));
@@ -84,7 +84,7 @@ LpOff plan_lp(Packer& P, const pmgl::LpLayout& L) {
 }
 
 pmgk::Lp2 bind_lp(const LpOff& o, char* base) {
-  return pmgk::Lp2{o.n, o.nx, o.nlines, o.nwin, o.lpr,
+  return pmgk::Lp2{o.n, o.nx, o.nlines, o.nwin, o.lpr, o.win,
                    reinterpret_cast<const int*>(base + o.wofs), reinterpret_cast<const int*>(base + o.wcol),
                    reinterpret_cast<const double*>(base + o.wval), reinterpret_cast<const int*>(base + o.waitofs),
                    reinterpret_cast<const int*>(base + o.wait), reinterpret_cast<const double*>(base + o.push),
@@ -296,14 +296,14 @@ void residual(Ctx& c, int l, const double* f, const double* u, double* r) {
 }
 
 // Line-pipelined solve launch (kLpLinesPerCta lines per CTA, two warps per line).
-template <bool MIR, bool UPD, int LPR>
+template <bool MIR, bool UPD, int WIN, int LPR>
 bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double* u) {
   const size_t smem = (size_t(2) * pmgk::kLpLinesPerCta * M.nx + size_t(pmgk::kLpLinesPerCta) * 2 * pmgk::kLpStage * 32) *
                       sizeof(double);
   if (smem > kLpSmemCap) return false;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(pmgk::k_lp2<MIR, UPD, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLpSmemCap));
+    cudaFuncSetAttribute(pmgk::k_lp2<MIR, UPD, WIN, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLpSmemCap));
     attr_set = true;
   }
   const int nblocks = (M.nlines + pmgk::kLpLinesPerCta - 1) / pmgk::kLpLinesPerCta;
@@ -311,18 +311,22 @@ bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double*
   unsigned* cnt = next_counter(c);
   // the output starts as "pending" (all-ones bytes); rows publish by overwriting it
   cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s);
-  pmgk::k_lp2<MIR, UPD, LPR><<<grid, 32 * (pmgk::kLpProducers + 1) * pmgk::kLpLinesPerCta, smem, c.s>>>(
+  pmgk::k_lp2<MIR, UPD, WIN, LPR><<<grid, 32 * (pmgk::kLpProducers + 1) * pmgk::kLpLinesPerCta, smem, c.s>>>(
       M, b, x, u, cnt, c.w->err);
   return true;
 }
 
-template <int LPR>
+template <int WIN, int LPR>
 bool lp_launch_l(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double* x, double* u) {
-  if (mirror) return u ? lp_launch_t<true, true, LPR>(c, M, b, x, u) : lp_launch_t<true, false, LPR>(c, M, b, x, u);
-  return u ? lp_launch_t<false, true, LPR>(c, M, b, x, u) : lp_launch_t<false, false, LPR>(c, M, b, x, u);
+  if (mirror) return u ? lp_launch_t<true, true, WIN, LPR>(c, M, b, x, u) : lp_launch_t<true, false, WIN, LPR>(c, M, b, x, u);
+  return u ? lp_launch_t<false, true, WIN, LPR>(c, M, b, x, u) : lp_launch_t<false, false, WIN, LPR>(c, M, b, x, u);
 }
+// Layouts the setup builds: ILUT factors (4 rows x 8 lanes), P1 sweeps (4 rows x 4 lanes).
 bool lp_launch(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double* x, double* u) {
-  return M.lpr == 4 ? lp_launch_l<4>(c, M, mirror, b, x, u) : lp_launch_l<1>(c, M, mirror, b, x, u);
+  if (M.win == 4 && M.lpr == 8) return lp_launch_l<4, 8>(c, M, mirror, b, x, u);
+  if (M.win == 8 && M.lpr == 1) return lp_launch_l<8, 1>(c, M, mirror, b, x, u);
+  if (M.win == 4 && M.lpr == 4) return lp_launch_l<4, 4>(c, M, mirror, b, x, u);
+  return false;
 }
 
 void lsolve(Ctx& c, int l, const double* b, double* y) {

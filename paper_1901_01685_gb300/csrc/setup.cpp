@@ -710,14 +710,15 @@ Csr strict_part(const Csr& a, bool lower) {
   return s;
 }
 
-LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lpr) {
+LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int win, int lpr) {
   LpLayout P;
   P.lpr = lpr;
-  const int lanes = kLpWin * lpr;
+  P.win = win;
+  const int lanes = win * lpr;
   P.n = M.nr;
   P.nx = nx;
   P.nlines = M.nr / nx;
-  P.nwin = (nx + kLpWin - 1) / kLpWin;
+  P.nwin = (nx + win - 1) / win;
   const int n = M.nr;
   P.dscale.assign(size_t(n), 1.0);
   if (dinv) {
@@ -728,8 +729,8 @@ LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lpr
   const int nwin_total = P.nlines * P.nwin;
   P.wofs.assign(size_t(nwin_total) + 1, 0);
   P.waitofs.assign(size_t(nwin_total) + 1, 0);
-  std::vector<std::vector<int>> far(size_t(kLpWin) * lpr);
-  std::vector<std::vector<double>> farv(size_t(kLpWin) * lpr);
+  std::vector<std::vector<int>> far(static_cast<size_t>(lanes));
+  std::vector<std::vector<double>> farv(static_cast<size_t>(lanes));
   for (int ln = 0; ln < P.nlines; ++ln) {
     for (int w = 0; w < P.nwin; ++w) {
       const int W = ln * P.nwin + w;
@@ -742,8 +743,8 @@ LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lpr
           if (q.first == dist) { q.second = std::max(q.second, local + 1); return; }
         need.emplace_back(dist, local + 1);
       };
-      for (int r = 0; r < kLpWin; ++r) {
-        const int ix = w * kLpWin + r;
+      for (int r = 0; r < win; ++r) {
+        const int ix = w * win + r;
         if (ix >= nx) break;
         const int i = ln * nx + ix;
         const int line_start = ln * nx;
@@ -866,11 +867,11 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
       L.Lsplit = line_split(L.L, L.n1d);
       L.Um = mirror(L.U);
       L.Umsplit = line_split(L.Um, L.n1d);
-      L.Llp = build_lp(L.L, L.n1d, nullptr, 4);
+      L.Llp = build_lp(L.L, L.n1d, nullptr, 4, 8);
       {
         std::vector<double> ud(size_t(L.N));
         for (int i = 0; i < L.N; ++i) ud[size_t(i)] = 1.0 / L.udiag[size_t(L.N - 1 - i)];
-        L.Ulp = build_lp(L.Um, L.n1d, &ud, 4);
+        L.Ulp = build_lp(L.Um, L.n1d, &ud, 4, 8);
       }
       H.t_ilut += ms_since(t0);
     }
@@ -908,11 +909,11 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
       Hl.UpM = mirror(Hl.Up);
       Hl.Losplit = line_split(Hl.Lo, Hl.n1d);
       Hl.UpMsplit = line_split(Hl.UpM, Hl.n1d);
-      Hl.Lolp = build_lp(Hl.Lo, Hl.n1d, &Hl.dinv, 1);
+      Hl.Lolp = build_lp(Hl.Lo, Hl.n1d, &Hl.dinv, 4, 4);
       {
         std::vector<double> dm(size_t(Hl.N));
         for (int i = 0; i < Hl.N; ++i) dm[size_t(i)] = Hl.dinv[size_t(Hl.N - 1 - i)];
-        Hl.UpMlp = build_lp(Hl.UpM, Hl.n1d, &dm, 1);
+        Hl.UpMlp = build_lp(Hl.UpM, Hl.n1d, &dm, 4, 4);
       }
     }
     {

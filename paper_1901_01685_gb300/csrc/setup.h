@@ -26,9 +26,9 @@ struct Csr {
 //  - "ring" part: entries in the row's own line at distance 1..31; stored by
 //    column j as push[j*32 + k-1] = M(j+k, j) d_{j+k} (zero if absent or if
 //    j+k lies in another line).
-//  - "far" part: all other entries, grouped in windows of kLpWin rows of one
+//  - "far" part: all other entries, grouped in windows of `win` rows of one
 //    line with `lpr` lanes per row: lane = lpr*r + s (r: row in window), slot k
-//    of lane l is entry s + lpr*k of that row, wcol/wval[wofs[w] + kLpWin*lpr*k
+//    of lane l is entry s + lpr*k of that row, wcol/wval[wofs[w] + win*lpr*k
 //    + l] (col -1 = padding).
 //  - wait list of window w: pairs (line distance, rows needed) in
 //    wait[waitofs[w] .. waitofs[w+1]).
@@ -36,12 +36,12 @@ struct Csr {
 struct LpLayout {
   int n = 0, nx = 0, nlines = 0, nwin = 0;    // nwin: windows per line
   int lpr = 1;                                 // lanes per row in the far part
+  int win = 8;                                 // rows per far-part window (win * lpr <= 32)
   std::vector<int> wofs, wcol, waitofs, wait;
   std::vector<double> wval, push, dscale;
   long long far_entries = 0, ring_entries = 0;
 };
-constexpr int kLpWin = 8;
-LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int lanes_per_row);
+LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int window_rows, int lanes_per_row);
 
 // One ILUT-smoothed level of degree q >= 2.
 struct PLevel {
