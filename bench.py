@@ -119,6 +119,22 @@ def _traffic(kernel_class: str):
     return None
 
 
+def reduce_step_time(t_local: float, dist, device) -> float:
+    """Max over ranks of the timed-region duration (replicas: the slowest rank sets
+    the job time).  `dist` is torch.distributed or None for a single process."""
+    if dist is None:
+        return t_local
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput: units all ranks processed / max-over-ranks time, in millions."""
+    return units_per_rank * world / t_max / 1e6
+
+
 def _oracle_sample(budget_s: float, degrees=(2, 3)):
     """The FP64 oracle (single host thread) on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -245,12 +261,8 @@ def run_ours(args):
     stats = [pmg.pmg_ws_stats(S.ws).as_dict() for S in solvers]
     for S in solvers:
         pmg.pmg_ws_profile(S.ws, False)
-    t_dev = sum(ev_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_dev = float(t.item())
-    value = units_total * world / t_dev / 1e6
+    t_dev = reduce_step_time(sum(ev_ms) / 1e3, dist, "cuda")
+    value = job_value(units_total, world, t_dev)
 
     # per-kernel-class totals over the timed region
     classes = {}
@@ -287,8 +299,8 @@ def run_ours(args):
             h2d += 2 * S.N * 8
             d2h += S.N * 8 + 8 * (it + 1) + 4 * it
     barrier()
-    t_e2e = time.perf_counter() - t0
-    e2e_value = e2e_units * world / t_e2e / 1e6
+    t_e2e = reduce_step_time(time.perf_counter() - t0, dist, "cuda")
+    e2e_value = job_value(e2e_units, world, t_e2e)
 
     if rank != 0:
         return

@@ -96,3 +96,25 @@ def test_l2_error_matches_oracle(pmg, oracle_mod):
         assert abs(pmg.pmg_l2_error(h, u) - oh.l2_error(u)) <= 1e-12 * oh.l2_error(u)
     finally:
         pmg.pmg_destroy(h)
+
+
+def test_calls_reject_null_and_out_of_order_arguments(pmg):
+    import ctypes as C
+    L = pmg.lib()
+    h = pmg.pmg_setup(0, 2, 3)
+    try:
+        # solve without a workspace / before upload
+        st = L.pmg_solve(h, None, None, None, 1e-8, 10, None, None, None, 0, None)
+        assert st == pmg.PMG_ERR_ARG
+        # upload into a buffer that is too small is refused before any device work
+        st = L.pmg_upload(h, C.c_void_p(256), 16, None)
+        assert st == pmg.PMG_ERR_ARG
+        # misaligned arena
+        info = pmg.pmg_info(h)
+        st = L.pmg_upload(h, C.c_void_p(257), info.device_bytes, None)
+        assert st == pmg.PMG_ERR_ARG
+        st = L.pmg_workspace_create(h, 0, None, 0, None, None)
+        assert st == pmg.PMG_ERR_ARG
+        assert pmg.pmg_last_error() != ""
+    finally:
+        pmg.pmg_destroy(h)
