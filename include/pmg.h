@@ -150,6 +150,28 @@ pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const d
                           double rel_tol, int max_iter, double* u_host, int* iters,
                           double* hist_host, int hist_cap, void* stream);
 
+/* Precision of the batched solve's inner V-cycle. */
+enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1 };
+
+/* Batched stand-alone solves of nrhs right-hand sides with one hierarchy.
+ * Each right-hand side follows the iteration u <- u + C(f - A u) of Sec. 5, C
+ * being one V-cycle with zero initial guess (the same affine map as the
+ * V-cycle of pmg_solve), until its own relative residual is below rel_tol (it
+ * is then frozen) or it diverges (> 1e10).  precision: PMG_PREC_FP64 runs the
+ * whole cycle in FP64; PMG_PREC_MIXED runs the residual-to-correction cycle on
+ * levels q >= 2 in FP32 (SpMV, triangular solves, transfers) inside the FP64
+ * defect-correction loop; the outer residual, the update of u and the p = 1
+ * coarse correction stay FP64.  F_dev, U0_dev, U_dev: nrhs x n[0] doubles,
+ * right-hand side k contiguous at offset k*n[0] (device).  The workspace must
+ * have been created with max_rhs >= max(nrhs, 2) (batched buffers).  iters_host[k]: cycles of
+ * right-hand side k; hist_host (may be NULL): max_iter x nrhs relative
+ * residuals, row = cycle.  Blocks until done.  Errors: PMG_ERR_ARG,
+ * PMG_ERR_MAXITER / PMG_ERR_DIVERGED (results still written), PMG_ERR_TIMEOUT,
+ * PMG_ERR_CUDA. */
+pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F_dev, const double* U0_dev,
+                             double rel_tol, int max_iter, int precision, double* U_dev, int* iters_host,
+                             double* hist_host, void* stream);
+
 /* Single steps of the cycle, for checking each one on its own.  `level` is a
  * p-level index (0 = degree p) for the first group and a P1 level index
  * (0 = h) for the second.  x, b: inputs; y: output (device).  Sizes follow

@@ -10,11 +10,13 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
 #include "../../include/pmg.h"
 #include "kernels.cuh"
+#include "kernels_batched.cuh"
 #include "setup.h"
 
 namespace {
@@ -100,6 +102,10 @@ struct DevPLevel {
   pmgk::Csr A{}, L{}, U{}, Pro{}, Res{};
   const double* udinv = nullptr;
   pmgk::Lp2 Llp{}, Ulp{};         // line-pipelined layouts (U mirrored)
+  // batched solves: FP32 copies for the inner cycle, plain CSR layouts
+  pmgk::TCsr<float> A32{}, Res32{}, Pro32{};
+  pmgk::LpB<double> Lb64{}, Ub64{};
+  pmgk::LpB<float> Lb32{}, Ub32{};
 };
 struct DevHLevel {
   int N = 0, ne = 0;
@@ -108,6 +114,7 @@ struct DevHLevel {
   const double* dinv = nullptr;
   pmgk::Lp2 Lolp{}, UpMlp{};
   double avg_lo = 0, avg_up = 0;
+  pmgk::LpB<double> Lob{}, UpMb{};   // batched Gauss-Seidel layouts
 };
 
 }  // namespace
@@ -120,6 +127,12 @@ struct pmg_hierarchy_s {
   std::vector<size_t> off_udinv, off_dinv;
   std::vector<DevCsrOff> off_Lo, off_Up;
   std::vector<LpOff> off_Llp, off_Ulp, off_Lolp, off_UpMlp;
+  // batched / mixed-precision data (host copies owned here until upload)
+  std::vector<std::vector<float>> f32store;
+  struct BOff { DevCsrOff Um; size_t A32, Res32, Pro32, L32, Um32, udm64, udm32; };
+  std::vector<BOff> boff;
+  struct HBOff { DevCsrOff UpM; size_t dinvM; };
+  std::vector<HBOff> hboff;
   size_t off_cinv = 0;
   bool uploaded = false;
   char* arena = nullptr;
@@ -136,6 +149,12 @@ struct pmg_workspace_s {
   std::vector<double*> f, u, r, y, e;
   // P1 levels
   std::vector<double*> hb, hx, hr, hg;
+  // batched solves (max_rhs > 1): [row][R] buffers, R = max_rhs rounded up to 32
+  int R = 0;
+  std::vector<double*> bf, be, br, by, bt;      // per p-level (reused as float for the inner cycle)
+  std::vector<double*> bhb, bhx, bhr, bhg, bht; // per P1 level (FP64)
+  double *bF = nullptr, *bU = nullptr, *bR = nullptr;
+  double *br0 = nullptr, *brel = nullptr, *bmask = nullptr, *bpart = nullptr;
   unsigned* flags = nullptr;
   unsigned long long* lprog = nullptr;   // per-line progress words of the line-pipelined solves
   unsigned* counters = nullptr;
@@ -168,6 +187,9 @@ struct WsLayout {
   size_t total = 0;
   std::vector<size_t> f, u, r, y, e, hb, hx, hr, hg;
   size_t flags, lprog, counters, err, partial, r0, hist, f_in, u_io;
+  int R = 0;
+  std::vector<size_t> bf, be, br, by, bt, bhb, bhx, bhr, bhg, bht;
+  size_t bF = 0, bU = 0, bR = 0, br0 = 0, brel = 0, bmask = 0, bpart = 0;
 };
 
 WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
@@ -177,15 +199,32 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
   const auto& H = h->H;
   int maxN = 0;
   for (const auto& L : H.lev) {
-    const size_t b = size_t(L.N) * sizeof(double) * max_rhs;
+    const size_t b = size_t(L.N) * sizeof(double);
     W.f.push_back(take(b)); W.u.push_back(take(b)); W.r.push_back(take(b));
     W.y.push_back(take(b)); W.e.push_back(take(b));
     maxN = std::max(maxN, L.N);
   }
   for (const auto& Hl : H.hl) {
-    const size_t b = size_t(Hl.N) * sizeof(double) * max_rhs;
+    const size_t b = size_t(Hl.N) * sizeof(double);
     W.hb.push_back(take(b)); W.hx.push_back(take(b)); W.hr.push_back(take(b)); W.hg.push_back(take(b));
     maxN = std::max(maxN, Hl.N);
+  }
+  if (max_rhs > 1) {
+    W.R = (max_rhs + 31) / 32 * 32;
+    for (const auto& L : H.lev) {
+      const size_t b = size_t(L.N) * sizeof(double) * W.R;
+      W.bf.push_back(take(b)); W.be.push_back(take(b)); W.br.push_back(take(b));
+      W.by.push_back(take(b)); W.bt.push_back(take(b));
+    }
+    for (const auto& Hl : H.hl) {
+      const size_t b = size_t(Hl.N) * sizeof(double) * W.R;
+      W.bhb.push_back(take(b)); W.bhx.push_back(take(b)); W.bhr.push_back(take(b));
+      W.bhg.push_back(take(b)); W.bht.push_back(take(b));
+    }
+    const size_t b0 = size_t(H.lev[0].N) * sizeof(double) * W.R;
+    W.bF = take(b0); W.bU = take(b0); W.bR = take(b0);
+    W.br0 = take(W.R * sizeof(double)); W.brel = take(W.R * sizeof(double)); W.bmask = take(W.R * sizeof(double));
+    W.bpart = take(size_t(pmgk::kNormBlocks) * W.R * sizeof(double));
   }
   W.flags = take(size_t(maxN) * sizeof(unsigned));
   int maxLines = 1;
@@ -197,8 +236,8 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
   W.partial = take(pmgk::kNormBlocks * sizeof(double));
   W.r0 = take(sizeof(double));
   W.hist = take(kHistCap * sizeof(double));
-  W.f_in = take(size_t(H.lev[0].N) * sizeof(double) * max_rhs);
-  W.u_io = take(size_t(H.lev[0].N) * sizeof(double) * max_rhs);
+  W.f_in = take(size_t(H.lev[0].N) * sizeof(double));
+  W.u_io = take(size_t(H.lev[0].N) * sizeof(double));
   W.total = s;
   return W;
 }
@@ -221,6 +260,16 @@ void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, doub
   } else {
     pmgk::k_spmv<8, MODE><<<grid_for((long long)A.nr * 8, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
   }
+}
+
+// Raises a kernel's dynamic shared-memory limit to kLpSmemCap once per device.
+void allow_smem(const void* fn) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.insert({fn, dev}).second) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLpSmemCap));
 }
 
 struct Ctx {
@@ -301,11 +350,7 @@ bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double*
   const size_t smem = (size_t(2) * pmgk::kLpLinesPerCta * M.nx + size_t(pmgk::kLpLinesPerCta) * 2 * pmgk::kLpStage * 32) *
                       sizeof(double);
   if (smem > kLpSmemCap) return false;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(pmgk::k_lp2<MIR, UPD, WIN, LPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kLpSmemCap));
-    attr_set = true;
-  }
+  allow_smem((const void*)pmgk::k_lp2<MIR, UPD, WIN, LPR>);
   const int nblocks = (M.nlines + pmgk::kLpLinesPerCta - 1) / pmgk::kLpLinesPerCta;
   const int grid = std::max(1, std::min(nblocks, c.h->sms));
   unsigned* cnt = next_counter(c);
@@ -532,6 +577,225 @@ pmg_status solve_impl(pmg_handle h, pmg_ws ws, const double* f, const double* u0
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// Batched solves: many right-hand sides, plain FP64 or an FP32 inner cycle
+// inside FP64 defect correction.  Vectors are [row][R] (right-hand sides
+// fastest, R a multiple of 32).  One iteration: r = f - A u (FP64), e = one
+// V-cycle with zero initial guess applied to r (inner precision T), u += e
+// (FP64) for the right-hand sides that have not converged yet.  The coarse
+// correction at p = 1 stays FP64 in both forms.
+// ---------------------------------------------------------------------------
+int grid_rows(long long work_warps, int sms) {
+  return grid_for(work_warps * 32, 256, sms * 16);
+}
+
+template <class TA, class TX, class TY, int MODE>
+void b_spmm(Ctx& c, int cls, const pmgk::TCsr<TA>& A, long long nnz, const TX* X, const TY* B, TY* Y) {
+  const int R = c.w->R;
+  launch(c, cls, 12.0 * nnz + 4.0 * (A.nr + 1) + (MODE == 1 ? 2.0 : 3.0) * A.nr * R * sizeof(TY), [&] {
+    pmgk::k_spmm<TA, TX, TY, MODE><<<grid_rows((long long)A.nr * (R / 32), c.h->sms), 256, 0, c.s>>>(A, R, X, B, Y);
+  });
+}
+pmgk::TCsr<double> as_t(const pmgk::Csr& a) { return pmgk::TCsr<double>{a.nr, a.rp, a.ci, a.v}; }
+
+template <class T>
+void b_lp(Ctx& c, int cls, const pmgk::LpB<T>& M, long long nnz, bool mirror, const T* b, T* x, T* u) {
+  const int R = c.w->R;
+  int lines = pmgk::kLpbMaxLines;
+  const size_t per_line = size_t(M.nx) * 32 * sizeof(T);
+  while (lines > 1 && lines * per_line > kLpSmemCap) --lines;
+  const size_t smem = lines * per_line;
+  const int nitems = ((M.nlines + lines - 1) / lines) * (R / 32);
+  const int grid = std::max(1, std::min(nitems, 2 * c.h->sms));
+  unsigned* cnt = next_counter(c);
+  launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + (u ? 4.0 : 2.0) * M.n * R * sizeof(T), [&] {
+    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
+    const int th = 32 * lines;
+    const int k = (mirror ? 2 : 0) + (u ? 1 : 0);
+    if (k == 0) { allow_smem((const void*)pmgk::k_lpb<T, false, false>); pmgk::k_lpb<T, false, false><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
+    if (k == 1) { allow_smem((const void*)pmgk::k_lpb<T, false, true>); pmgk::k_lpb<T, false, true><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
+    if (k == 2) { allow_smem((const void*)pmgk::k_lpb<T, true, false>); pmgk::k_lpb<T, true, false><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
+    if (k == 3) { allow_smem((const void*)pmgk::k_lpb<T, true, true>); pmgk::k_lpb<T, true, true><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
+  });
+}
+
+template <class TI, class TO>
+void b_cast(Ctx& c, long long n, const TI* x, TO* y) {
+  pmgk::k_cast<TI, TO><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
+  ++c.w->launches;
+}
+
+// Gauss-Seidel sweep, batched: the old-value part as an SpMM, the new values by the line-pipelined solve.
+void b_gs(Ctx& c, int j, bool backward, const double* b, double* x) {
+  const DevHLevel& D = c.h->dh[j];
+  const int R = c.w->R;
+  double* t = c.w->bht[j];
+  double* xn = c.w->bhg[j];
+  if (backward) b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Lo), D.nnzA / 2, x, b, t);
+  else b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Up), D.nnzA / 2, x, b, t);
+  b_lp<double>(c, PMG_K_GS, backward ? D.UpMb : D.Lob, D.nnzA / 2, backward, t, xn, nullptr);
+  cudaMemcpyAsync(x, xn, size_t(D.N) * R * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+}
+
+void b_hmg(Ctx& c, int j, const double* b, double* x) {
+  const int nh = int(c.h->dh.size()), R = c.w->R;
+  const DevHLevel& D = c.h->dh[j];
+  if (j == nh - 1) {
+    launch(c, PMG_K_COARSE, 8.0 * D.N * D.N + 16.0 * D.N * R, [&] {
+      pmgk::k_dense_mm<<<grid_rows((long long)D.N * (R / 32), c.h->sms), 256, 0, c.s>>>(D.N, R, c.h->cinv, b, x);
+    });
+    return;
+  }
+  const DevHLevel& Cc = c.h->dh[j + 1];
+  const int d = c.h->H.d;
+  b_gs(c, j, false, b, x);
+  b_spmm<double, double, double, 0>(c, PMG_K_P1, as_t(D.A), D.nnzA, x, b, c.w->bhr[j]);
+  launch(c, PMG_K_P1, 8.0 * (D.N + Cc.N) * R, [&] {
+    pmgk::k_p1_restrict_b<<<grid_for((long long)Cc.N * R, 256, c.h->sms * 16), 256, 0, c.s>>>(d, D.ne, R, c.w->bhr[j], c.w->bhb[j + 1]);
+  });
+  cudaMemsetAsync(c.w->bhx[j + 1], 0, size_t(Cc.N) * R * sizeof(double), c.s);
+  b_hmg(c, j + 1, c.w->bhb[j + 1], c.w->bhx[j + 1]);
+  launch(c, PMG_K_P1, (8.0 * Cc.N + 16.0 * D.N) * R, [&] {
+    pmgk::k_p1_prolong_add_b<<<grid_for((long long)D.N * R, 256, c.h->sms * 16), 256, 0, c.s>>>(d, D.ne, R, c.w->bhx[j + 1], x);
+  });
+  b_gs(c, j, true, b, x);
+}
+
+// e = one V-cycle at p-level l applied to the right-hand side f with zero initial guess (precision T).
+template <class T>
+void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
+  const auto& H = c.h->H;
+  const DevPLevel& D = c.h->dl[l];
+  const int nlev = int(c.h->dl.size()), R = c.w->R;
+  const pmgk::TCsr<T> A = [&] {
+    if constexpr (sizeof(T) == 4) return D.A32; else return as_t(D.A);
+  }();
+  const pmgk::LpB<T>& Lb = [&]() -> const pmgk::LpB<T>& {
+    if constexpr (sizeof(T) == 4) return D.Lb32; else return D.Lb64;
+  }();
+  const pmgk::LpB<T>& Ub = [&]() -> const pmgk::LpB<T>& {
+    if constexpr (sizeof(T) == 4) return D.Ub32; else return D.Ub64;
+  }();
+  const pmgk::TCsr<T> Res = [&] {
+    if constexpr (sizeof(T) == 4) return D.Res32; else return as_t(D.Res);
+  }();
+  const pmgk::TCsr<T> Pro = [&] {
+    if constexpr (sizeof(T) == 4) return D.Pro32; else return as_t(D.Pro);
+  }();
+  T* r = reinterpret_cast<T*>(c.w->br[l]);
+  T* y = reinterpret_cast<T*>(c.w->by[l]);
+  T* t = reinterpret_cast<T*>(c.w->bt[l]);
+  const size_t nR = size_t(D.N) * R;
+  cudaMemsetAsync(e, 0, nR * sizeof(T), c.s);
+  auto smooth = [&](bool first) {
+    const T* rr = f;
+    if (!first) { b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r); rr = r; }
+    b_lp<T>(c, PMG_K_LSOLVE, Lb, D.nnzL, false, rr, y, nullptr);
+    b_lp<T>(c, PMG_K_USOLVE, Ub, D.nnzU, true, y, t, e);
+  };
+  for (int m = 0; m < H.opt.nu_pre; ++m) smooth(m == 0);
+  b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r);
+  if (l + 1 < nlev) {
+    T* fc = reinterpret_cast<T*>(c.w->bf[l + 1]);
+    T* ec = reinterpret_cast<T*>(c.w->be[l + 1]);
+    b_spmm<T, T, T, 1>(c, PMG_K_TRANSFER, Res, D.nnzP, r, nullptr, fc);
+    b_vcycle0<T>(c, l + 1, fc, ec);
+    b_spmm<T, T, T, 2>(c, PMG_K_TRANSFER, Pro, D.nnzP, ec, e, e);
+  } else {
+    const int N1 = c.h->dh[0].N;
+    double* b1 = c.w->bhb[0];
+    double* x1 = c.w->bhx[0];
+    if constexpr (sizeof(T) == 4) {
+      float* fc = reinterpret_cast<float*>(c.w->bhr[0]);   // restricted residual before widening
+      b_spmm<float, float, float, 1>(c, PMG_K_TRANSFER, Res, D.nnzP, r, nullptr, fc);
+      b_cast<float, double>(c, (long long)N1 * R, fc, b1);
+    } else {
+      b_spmm<double, double, double, 1>(c, PMG_K_TRANSFER, Res, D.nnzP, r, nullptr, b1);
+    }
+    cudaMemsetAsync(x1, 0, size_t(N1) * R * sizeof(double), c.s);
+    for (int k = 0; k < H.opt.coarse_cycles; ++k) b_hmg(c, 0, b1, x1);
+    if constexpr (sizeof(T) == 4) {
+      float* ec = reinterpret_cast<float*>(c.w->bhg[0]);
+      b_cast<double, float>(c, (long long)N1 * R, x1, ec);
+      b_spmm<float, float, float, 2>(c, PMG_K_TRANSFER, Pro, D.nnzP, ec, e, e);
+    } else {
+      b_spmm<double, double, double, 2>(c, PMG_K_TRANSFER, Pro, D.nnzP, x1, e, e);
+    }
+  }
+  for (int m = 0; m < H.opt.nu_post; ++m) smooth(false);
+}
+
+void b_norms(Ctx& c, int n, const double* r, int mode) {
+  const int R = c.w->R;
+  launch(c, PMG_K_NORM, 8.0 * n * R, [&] {
+    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(n, R, r, c.w->bpart);
+    if (mode == 0) pmgk::k_norm_finalize_b<0><<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, c.w->bpart, c.w->br0, nullptr);
+    else pmgk::k_norm_finalize_b<1><<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, c.w->bpart, c.w->br0, c.w->brel);
+  });
+}
+
+pmg_status solve_batched_impl(pmg_handle h, pmg_ws ws, int nrhs, const double* F, const double* U0, double tol,
+                              int max_iter, int precision, double* Uout, int* iters, double* hist,
+                              cudaStream_t s) {
+  Ctx c{h, ws, s};
+  const int N = h->dl[0].N, R = ws->R;
+  const DevPLevel& D = h->dl[0];
+  std::vector<double> r0(R), rel(R), mask(R, 0.0);
+  std::vector<int> done(nrhs, 0);
+  for (int k = 0; k < nrhs; ++k) iters[k] = 0;
+  pmg_status st = begin_launches(c);
+  if (st != PMG_OK) return st;
+  pmgk::k_to_rows<<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, F, ws->bF);
+  pmgk::k_to_rows<<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, U0, ws->bU);
+  ws->launches += 2;
+  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+  b_norms(c, N, ws->bR, 0);
+  PMG_CUDA(cudaMemcpyAsync(r0.data(), ws->br0, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+  st = finish_launches(c);
+  if (st != PMG_OK) return st;
+  int active = 0;
+  for (int k = 0; k < nrhs; ++k) {
+    if (r0[k] > 0.0) { mask[k] = 1.0; ++active; } else done[k] = 1;
+  }
+  pmg_status result = PMG_OK;
+  for (int it = 0; it < max_iter && active > 0; ++it) {
+    st = begin_launches(c);
+    if (st != PMG_OK) return st;
+    PMG_CUDA(cudaMemcpyAsync(ws->bmask, mask.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (precision == PMG_PREC_MIXED) {
+      float* r32 = reinterpret_cast<float*>(ws->bf[0]);
+      float* e32 = reinterpret_cast<float*>(ws->be[0]);
+      b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
+      b_vcycle0<float>(c, 0, r32, e32);
+      pmgk::k_masked_update<float><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, R, e32, ws->bmask, ws->bU);
+    } else {
+      double* e64 = ws->be[0];
+      b_vcycle0<double>(c, 0, ws->bR, e64);
+      pmgk::k_masked_update<double><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, R, e64, ws->bmask, ws->bU);
+    }
+    ++ws->launches;
+    b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+    b_norms(c, N, ws->bR, 1);
+    PMG_CUDA(cudaMemcpyAsync(rel.data(), ws->brel, R * sizeof(double), cudaMemcpyDeviceToHost, s));
+    st = finish_launches(c);
+    if (st != PMG_OK) return st;
+    for (int k = 0; k < nrhs; ++k) {
+      if (done[k]) continue;
+      if (hist) hist[(size_t)it * nrhs + k] = rel[k];
+      iters[k] = it + 1;
+      if (rel[k] < tol) { done[k] = 1; mask[k] = 0.0; --active; }
+      else if (!(rel[k] <= 1e10)) { done[k] = 1; mask[k] = 0.0; --active; result = PMG_ERR_DIVERGED; }
+    }
+  }
+  if (active > 0 && result == PMG_OK) { result = PMG_ERR_MAXITER; g_last_error = "maximum number of V-cycles reached"; }
+  if (result == PMG_ERR_DIVERGED) g_last_error = "relative residual exceeded 1e10 for a right-hand side";
+  pmgk::k_from_rows<<<grid_for((long long)N * nrhs, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, ws->bU, Uout);
+  ++ws->launches;
+  PMG_CUDA(cudaGetLastError());
+  PMG_CUDA(cudaStreamSynchronize(s));
+  return result;
+}
+
 }  // namespace
 
 extern "C" {
@@ -590,6 +854,33 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     h->off_UpMlp.push_back(plan_lp(P, Hl.UpMlp));
   }
   h->off_cinv = P.add(h->H.coarse_inv.data(), h->H.coarse_inv.size() * sizeof(double));
+  // FP32 copies (inner cycle of the mixed-precision batched solve) and CSR
+  // layouts of the mirrored factors for the batched line-pipelined solve
+  auto f32 = [&](const std::vector<double>& v) {
+    h->f32store.emplace_back(v.begin(), v.end());
+    const auto& w = h->f32store.back();
+    return P.add(w.data(), w.size() * sizeof(float));
+  };
+  h->f32store.reserve(8 * h->H.lev.size() + 8);
+  for (size_t l = 0; l < h->H.lev.size(); ++l) {
+    const auto& L = h->H.lev[l];
+    pmg_hierarchy_s::BOff b;
+    b.Um = plan_csr(P, L.Um);
+    b.A32 = f32(L.A.v);
+    b.Res32 = f32(L.Res.v);
+    b.Pro32 = f32(L.Pro.v);
+    b.L32 = f32(L.L.v);
+    b.Um32 = f32(L.Um.v);
+    b.udm64 = P.add(L.Ulp.dscale.data(), L.Ulp.dscale.size() * sizeof(double));
+    b.udm32 = f32(L.Ulp.dscale);
+    h->boff.push_back(b);
+  }
+  for (const auto& Hl : h->H.hl) {
+    pmg_hierarchy_s::HBOff b;
+    b.UpM = plan_csr(P, Hl.UpM);
+    b.dinvM = P.add(Hl.UpMlp.dscale.data(), Hl.UpMlp.dscale.size() * sizeof(double));
+    h->hboff.push_back(b);
+  }
   *out = h;
   return PMG_OK;
 }
@@ -682,6 +973,20 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.nnzP = h->off_Pro[l].nnz;
     D.Llp = bind_lp(h->off_Llp[l], base);
     D.Ulp = bind_lp(h->off_Ulp[l], base);
+    {
+      const auto& b = h->boff[l];
+      const int nx = h->H.lev[l].n1d;
+      auto fp = [&](size_t off) { return reinterpret_cast<const float*>(base + off); };
+      D.A32 = pmgk::TCsr<float>{D.A.nr, D.A.rp, D.A.ci, fp(b.A32)};
+      D.Res32 = pmgk::TCsr<float>{D.Res.nr, D.Res.rp, D.Res.ci, fp(b.Res32)};
+      D.Pro32 = pmgk::TCsr<float>{D.Pro.nr, D.Pro.rp, D.Pro.ci, fp(b.Pro32)};
+      const pmgk::Csr Um = bind(b.Um, base);
+      D.Lb64 = pmgk::LpB<double>{D.N, nx, D.N / nx, D.L.rp, D.L.ci, D.L.v, nullptr};
+      D.Ub64 = pmgk::LpB<double>{D.N, nx, D.N / nx, Um.rp, Um.ci, Um.v,
+                                 reinterpret_cast<const double*>(base + b.udm64)};
+      D.Lb32 = pmgk::LpB<float>{D.N, nx, D.N / nx, D.L.rp, D.L.ci, fp(b.L32), nullptr};
+      D.Ub32 = pmgk::LpB<float>{D.N, nx, D.N / nx, Um.rp, Um.ci, fp(b.Um32), fp(b.udm32)};
+    }
     h->dl.push_back(D);
   }
   for (size_t j = 0; j < h->H.hl.size(); ++j) {
@@ -695,6 +1000,13 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.Up = bind(h->off_Up[j], base);
     D.Lolp = bind_lp(h->off_Lolp[j], base);
     D.UpMlp = bind_lp(h->off_UpMlp[j], base);
+    {
+      const int nx = h->H.hl[j].n1d;
+      const pmgk::Csr UpM = bind(h->hboff[j].UpM, base);
+      D.Lob = pmgk::LpB<double>{D.N, nx, D.N / nx, D.Lo.rp, D.Lo.ci, D.Lo.v, D.dinv};
+      D.UpMb = pmgk::LpB<double>{D.N, nx, D.N / nx, UpM.rp, UpM.ci, UpM.v,
+                                 reinterpret_cast<const double*>(base + h->hboff[j].dinvM)};
+    }
     D.avg_lo = double(h->off_Lo[j].nnz) / std::max(1, D.N);
     D.avg_up = double(h->off_Up[j].nnz) / std::max(1, D.N);
     h->dh.push_back(D);
@@ -735,6 +1047,19 @@ pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t byt
   for (size_t j = 0; j < W.hb.size(); ++j) {
     w->hb.push_back(P(W.hb[j])); w->hx.push_back(P(W.hx[j])); w->hr.push_back(P(W.hr[j]));
     w->hg.push_back(P(W.hg[j]));
+  }
+  w->R = W.R;
+  for (size_t l = 0; l < W.bf.size(); ++l) {
+    w->bf.push_back(P(W.bf[l])); w->be.push_back(P(W.be[l])); w->br.push_back(P(W.br[l]));
+    w->by.push_back(P(W.by[l])); w->bt.push_back(P(W.bt[l]));
+  }
+  for (size_t j = 0; j < W.bhb.size(); ++j) {
+    w->bhb.push_back(P(W.bhb[j])); w->bhx.push_back(P(W.bhx[j])); w->bhr.push_back(P(W.bhr[j]));
+    w->bhg.push_back(P(W.bhg[j])); w->bht.push_back(P(W.bht[j]));
+  }
+  if (W.R) {
+    w->bF = P(W.bF); w->bU = P(W.bU); w->bR = P(W.bR);
+    w->br0 = P(W.br0); w->brel = P(W.brel); w->bmask = P(W.bmask); w->bpart = P(W.bpart);
   }
   w->flags = reinterpret_cast<unsigned*>(base + W.flags);
   w->lprog = reinterpret_cast<unsigned long long*>(base + W.lprog);
@@ -777,6 +1102,17 @@ pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const d
   PMG_CUDA(cudaStreamSynchronize(s));
   g_last_error = keep;
   return st;
+}
+
+pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F, const double* U0, double tol,
+                             int max_iter, int precision, double* U, int* iters, double* hist, void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  if (nrhs < 1 || nrhs > ws->max_rhs || ws->R == 0 || !F || !U0 || !U || !iters || max_iter < 1 || !(tol > 0) ||
+      (precision != PMG_PREC_FP64 && precision != PMG_PREC_MIXED))
+    return fail(PMG_ERR_ARG, "invalid batched solve argument (workspace holds " + std::to_string(ws->R ? ws->max_rhs : 0) + " right-hand sides)");
+  return solve_batched_impl(h, ws, nrhs, F, U0, tol, max_iter, precision, U, iters, hist,
+                            static_cast<cudaStream_t>(stream));
 }
 
 pmg_status pmg_apply(pmg_handle h, pmg_ws ws, int op, int level, const double* x, const double* b, double* y,

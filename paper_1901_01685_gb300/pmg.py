@@ -27,10 +27,12 @@ PMG_PROJ_INDIRECT, PMG_PROJ_DIRECT = 0, 1
 (PMG_OP_RESIDUAL, PMG_OP_SMOOTH, PMG_OP_LSOLVE, PMG_OP_USOLVE, PMG_OP_RESTRICT, PMG_OP_PROLONG_ADD,
  PMG_OP_COARSE_SOLVE, PMG_OP_VCYCLE, PMG_OP_GS_FWD, PMG_OP_GS_BWD, PMG_OP_HMG_VCYCLE) = range(11)
 PMG_MAX_LEVELS = 16
+PMG_PREC_FP64, PMG_PREC_MIXED = 0, 1
 
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
-           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_apply", "pmg_export_csr",
+           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_apply",
+           "pmg_export_csr",
            "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_lsolve_noalloc",
            "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
 PMG_NKERN = 8
@@ -100,6 +102,7 @@ def lib():
         L.pmg_workspace_create.argtypes = [vp, C.c_int, vp, C.c_size_t, vp, C.POINTER(vp)]
         L.pmg_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
         L.pmg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, dp, ip, dp, C.c_int, vp]
+        L.pmg_solve_batched.argtypes = [vp, vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int, vp, ip, dp, vp]
         L.pmg_apply.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
         L.pmg_export_csr.argtypes = [vp, C.c_int, C.c_int, ip, ip, C.POINTER(C.c_longlong), ip, ip, dp]
         L.pmg_export_lumped.argtypes = [vp, C.c_int, dp]
@@ -218,6 +221,17 @@ def pmg_solve_host(h, ws, f: np.ndarray, u0: np.ndarray, rel_tol, max_iter, u: n
     return iters.value, hist[: min(iters.value, hist_cap)].copy(), st
 
 
+def pmg_solve_batched(h, ws, nrhs, F, U0, rel_tol, max_iter, precision, U, stream=None, allow=()):
+    """F, U0, U: device tensors of nrhs x n doubles (right-hand side k in row k).
+    Returns (iters per right-hand side, history [cycles x nrhs], status)."""
+    iters = np.zeros(nrhs, np.int32)
+    hist = np.zeros((max_iter, nrhs))
+    st = lib().pmg_solve_batched(h, ws, nrhs, _ptr(F), _ptr(U0), rel_tol, max_iter, precision, _ptr(U),
+                                 _ip(iters), _dp(hist), _stream(stream))
+    _check(st, "pmg_solve_batched", allow)
+    return iters, hist[: int(iters.max(initial=0))].copy(), st
+
+
 def pmg_apply(h, ws, op, level, x, b, y, stream=None):
     _check(lib().pmg_apply(h, ws, op, level, _ptr(x), _ptr(b), _ptr(y), _stream(stream)), "pmg_apply")
 
@@ -284,7 +298,7 @@ class Solver:
     def __init__(self, domain: int, p: int, log2_inv_h: int, projection: int = PMG_PROJ_INDIRECT,
                  exact: int = PMG_U_SINPROD, drop_tol: float = 1e-12, fill_factor: float = 1.0,
                  nu_pre: int = 1, nu_post: int = 1, coarse_cycles: int = 2, device: str = "cuda",
-                 upload: bool = True):
+                 upload: bool = True, max_rhs: int = 1):
         opt = pmg_default_options()
         opt.projection, opt.exact, opt.drop_tol, opt.fill_factor = projection, exact, drop_tol, fill_factor
         opt.nu_pre, opt.nu_post, opt.coarse_cycles = nu_pre, nu_post, coarse_cycles
@@ -292,6 +306,7 @@ class Solver:
         self.info = pmg_info(self.h).as_dict()
         self.N = self.info["n"][0]
         self.arena = self.mem = self.ws = None
+        self.max_rhs = max_rhs
         if upload:
             self.upload(device)
 
@@ -300,9 +315,9 @@ class Solver:
         nbytes = max(self.info["device_bytes"], 256)
         self.arena = torch.empty((nbytes + 255) // 256 * 32, dtype=torch.float64, device=device)
         pmg_upload(self.h, self.arena)
-        wb = pmg_workspace_bytes(self.h, 1)
+        wb = pmg_workspace_bytes(self.h, self.max_rhs)
         self.mem = torch.empty((wb + 255) // 256 * 32, dtype=torch.float64, device=device)
-        self.ws = pmg_workspace_create(self.h, 1, self.mem)
+        self.ws = pmg_workspace_create(self.h, self.max_rhs, self.mem)
 
     def rhs(self) -> np.ndarray:
         return pmg_rhs(self.h, self.N)
@@ -313,6 +328,15 @@ class Solver:
             u = torch.empty_like(u0)
         it, hist, st = pmg_solve(self.h, self.ws, f, u0, rel_tol, max_iter, u, allow=allow)
         return u, it, hist, st
+
+    def solve_batched(self, F, U0, rel_tol=1e-8, max_iter=100, precision=PMG_PREC_FP64, U=None, allow=()):
+        """F, U0: (nrhs, n) float64 device tensors.  Returns (U, iters, hist, status)."""
+        import torch
+        if U is None:
+            U = torch.empty_like(U0)
+        it, hist, st = pmg_solve_batched(self.h, self.ws, F.shape[0], F, U0, rel_tol, max_iter, precision, U,
+                                         allow=allow)
+        return U, it, hist, st
 
     def apply(self, op, level, x, b, y):
         pmg_apply(self.h, self.ws, op, level, x, b, y)

@@ -1,0 +1,170 @@
+"""Batched solves (many right-hand sides per hierarchy) through the C-ABI.
+
+Plain FP64: every right-hand side is checked against the FP64 oracle's own
+solve of it, with the single-solve tolerances (the batched iteration
+u <- u + C(f - A u) is the same affine map as the V-cycle with initial guess u,
+Sec. 5, so only rounding differs):
+  relative residual history: |difference| <= 1e-12 per V-cycle
+  iteration count:          equal within 1
+  final solution:           ||u_gpu - u_oracle|| / ||u_oracle|| <= 1e-10
+
+FP32 inner cycle inside FP64 defect correction: the iteration converges to the
+same FP64 stopping criterion.  Its relative residual is recomputed by the
+oracle from the returned u (it must be below 1e-8 up to rounding of the
+residual itself, 1e-8 * (1 + 1e-6)), and it needs at most two cycles more than
+the FP64 oracle: single precision only perturbs the preconditioner C by a
+relative O(1e-7), which leaves its contraction factor (~0.1 or smaller for
+these cases) practically unchanged.
+"""
+import numpy as np
+import pytest
+
+from paper_1901_01685_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+HIST_TOL = 1e-12
+U_TOL = 1e-10
+RELRES_SLACK = 1e-8 * (1 + 1e-6)
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def pmg():
+    from paper_1901_01685_gb300 import pmg as P
+    P.lib()
+    return P
+
+
+_cache = {}
+
+
+def _pair(pmg, oracle_mod, dom, p, k, proj=0, max_rhs=40):
+    key = (dom, p, k, proj, max_rhs)
+    if key not in _cache:
+        S = pmg.Solver(dom, p, k, projection=proj, max_rhs=max_rhs)
+        O = oracle_mod.Hierarchy(dom, p, k, projection=proj)
+        _cache[key] = (S, O)
+    return _cache[key]
+
+
+def _dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _batch(O, nrhs, seed=2):
+    F = inputs.batched_rhs(O.rhs(), nrhs, seed=seed)
+    U0 = np.stack([inputs.initial_guess(O.N[0], 100 + r) for r in range(nrhs)])
+    return F, U0
+
+
+def _relres(O, f, u, u0):
+    return np.linalg.norm(O.residual(0, f, u)) / np.linalg.norm(O.residual(0, f, u0))
+
+
+CASES = [(0, 3, 5, 0), (1, 2, 5, 0), (2, 2, 3, 0), (0, 4, 6, 1)]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_batched_fp64_matches_oracle_per_rhs(torch_mod, pmg, oracle_mod, case):
+    torch = torch_mod
+    S, O = _pair(pmg, oracle_mod, *case)
+    nrhs = 5                           # one partly filled group of 32 right-hand sides
+    F, U0 = _batch(O, nrhs)
+    U, it, hist, st = S.solve_batched(_dev(torch, F), _dev(torch, U0), precision=pmg.PMG_PREC_FP64)
+    assert st == 0
+    Un = U.cpu().numpy()
+    for r in range(nrhs):
+        uo, ho, ito, sto = O.solve(F[r], U0[r])
+        assert sto == "ok"
+        assert abs(it[r] - ito) <= 1, (r, it[r], ito)
+        m = min(it[r], ito)
+        assert np.abs(hist[:m, r] - ho[:m]).max() <= HIST_TOL, (r, hist[:, r], ho)
+        assert np.linalg.norm(Un[r] - uo) <= U_TOL * np.linalg.norm(uo)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_batched_mixed_precision_reaches_fp64_tolerance(torch_mod, pmg, oracle_mod, case):
+    torch = torch_mod
+    S, O = _pair(pmg, oracle_mod, *case)
+    nrhs = 7
+    F, U0 = _batch(O, nrhs, seed=9)
+    U, it, hist, st = S.solve_batched(_dev(torch, F), _dev(torch, U0), precision=pmg.PMG_PREC_MIXED)
+    assert st == 0
+    Un = U.cpu().numpy()
+    for r in range(nrhs):
+        assert hist[it[r] - 1, r] < 1e-8
+        assert _relres(O, F[r], Un[r], U0[r]) < RELRES_SLACK
+        ito = O.solve(F[r], U0[r])[2]
+        assert it[r] <= ito + 2, (r, it[r], ito)
+
+
+def test_rhs_result_does_not_depend_on_its_batch(torch_mod, pmg, oracle_mod):
+    """Right-hand side arithmetic is per lane: the same right-hand side gives
+    bit-identical results alone, in a full group and in the second group."""
+    torch = torch_mod
+    S, O = _pair(pmg, oracle_mod, 0, 3, 5, 0)
+    F, U0 = _batch(O, 40, seed=4)
+    for prec in (pmg.PMG_PREC_FP64, pmg.PMG_PREC_MIXED):
+        Ub, itb, hb, _ = S.solve_batched(_dev(torch, F), _dev(torch, U0), precision=prec)
+        k = 33
+        Ua, ita, ha, _ = S.solve_batched(_dev(torch, F[k:k + 1]), _dev(torch, U0[k:k + 1]), precision=prec)
+        assert ita[0] == itb[k]
+        assert np.array_equal(ha[:, 0], hb[: ita[0], k])
+        assert torch.equal(Ua[0], Ub[k])
+
+
+def test_converged_rhs_are_frozen(torch_mod, pmg, oracle_mod):
+    """A right-hand side whose initial guess already solves it stops at once and
+    keeps u0 while the others iterate."""
+    torch = torch_mod
+    S, O = _pair(pmg, oracle_mod, 1, 2, 5, 0)
+    F, U0 = _batch(O, 3, seed=6)
+    F[1] = 0.0
+    U0[1] = 0.0
+    U, it, hist, st = S.solve_batched(_dev(torch, F), _dev(torch, U0))
+    assert st == 0 and it[1] == 0 and it[0] > 0 and it[2] > 0
+    assert torch.count_nonzero(U[1]).item() == 0
+
+
+def test_batched_argument_checks(torch_mod, pmg, oracle_mod):
+    torch = torch_mod
+    S, O = _pair(pmg, oracle_mod, 1, 2, 5, 0)
+    F, U0 = _batch(O, 41)
+    with pytest.raises(pmg.PmgError) as e:
+        S.solve_batched(_dev(torch, F), _dev(torch, U0))       # the workspace holds 40
+    assert e.value.status == pmg.PMG_ERR_ARG
+    with pytest.raises(pmg.PmgError) as e:
+        S.solve_batched(_dev(torch, F[:2]), _dev(torch, U0[:2]), precision=7)
+    assert e.value.status == pmg.PMG_ERR_ARG
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_batched_full_size_annulus(torch_mod, pmg, oracle_mod, p):
+    """Quarter annulus at h = 2^-8 (~66k unknowns), 64 right-hand sides: FP64
+    against the oracle on sampled right-hand sides; the mixed form reaches the
+    FP64 tolerance (checked by the oracle's residual) on the same samples."""
+    torch = torch_mod
+    S = pmg.Solver(0, p, 8, max_rhs=64)
+    O = oracle_mod.Hierarchy(0, p, 8)
+    F, U0 = _batch(O, 64, seed=12)
+    Fd, U0d = _dev(torch, F), _dev(torch, U0)
+    U, it, hist, st = S.solve_batched(Fd, U0d, precision=pmg.PMG_PREC_FP64)
+    Um, itm, histm, stm = S.solve_batched(Fd, U0d, precision=pmg.PMG_PREC_MIXED)
+    assert st == 0 and stm == 0
+    Un, Umn = U.cpu().numpy(), Um.cpu().numpy()
+    for r in (0, 37, 63):
+        uo, ho, ito, sto = O.solve(F[r], U0[r])
+        assert abs(it[r] - ito) <= 1
+        m = min(it[r], ito)
+        assert np.abs(hist[:m, r] - ho[:m]).max() <= HIST_TOL
+        assert np.linalg.norm(Un[r] - uo) <= U_TOL * np.linalg.norm(uo)
+        assert _relres(O, F[r], Umn[r], U0[r]) < RELRES_SLACK
+        assert itm[r] <= ito + 2
