@@ -31,6 +31,8 @@ METRIC = "MDOF*iter/s to 1e-8 relres (plain FP64)"
 UNIT = "MDOF*iter/s"
 DEGREES = (2, 3, 4, 5)
 LOG2H = 8
+BATCHED_CASE = (0, 4, 9)     # quarter annulus, p = 4, h = 2^-9
+BATCHED_NRHS = 64
 WORKLOAD = "quarter annulus Poisson, h=2^-8, p=2..5, indirect p-MG V-cycle, ILUT(1e-12,1), 1e-8 relres"
 
 
@@ -188,6 +190,68 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _batched_section(args, dist, flush, stream, world):
+    """Many right-hand sides on one hierarchy: plain FP64 single solves, the
+    batched FP64 solve and the batched FP32-inner / FP64-defect-correction solve
+    of the same right-hand sides, each timed with CUDA events (L2 flushed
+    before every timed solve)."""
+    import numpy as np
+    import torch
+    from paper_1901_01685_gb300 import inputs, pmg
+
+    dom, p, k = BATCHED_CASE
+    S = pmg.Solver(dom, p, k, max_rhs=BATCHED_NRHS)
+    N = S.N
+    F = torch.as_tensor(inputs.batched_rhs(S.rhs(), BATCHED_NRHS, seed=2), device="cuda")
+    U0 = torch.as_tensor(np.stack([inputs.initial_guess(N, 1)] * BATCHED_NRHS), device="cuda")
+    U = torch.empty_like(U0)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms, out = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return reduce_step_time(sum(ms) / 1e3, dist, "cuda") / args.steps, out
+
+    u1 = torch.empty(N, dtype=torch.float64, device="cuda")
+    t_single, single = timed(lambda: S.solve(F[0], U0[0], u=u1)[1])
+    res = {}
+    for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED)):
+        t, it = timed(lambda: S.solve_batched(F, U0, precision=prec, U=U)[1])
+        res[name] = {"ms_per_batch": 1e3 * t, "solves_per_s": world * BATCHED_NRHS / t,
+                     "MDOF_iter_per_s": world * N * int(np.sum(it)) / t / 1e6,
+                     "iterations": [int(it.min()), int(it.max())], "u": U.clone()}
+    # the mixed form against the FP64 form (itself checked against the FP64 oracle by the tests)
+    du = (res["mixed"]["u"] - res["fp64"]["u"]).norm(dim=1) / res["fp64"]["u"].norm(dim=1)
+    relres = []
+    for r in range(BATCHED_NRHS):
+        rr = torch.empty(N, dtype=torch.float64, device="cuda")
+        S.apply(pmg.PMG_OP_RESIDUAL, 0, res["mixed"]["u"][r], F[r], rr)
+        r0 = torch.empty(N, dtype=torch.float64, device="cuda")
+        S.apply(pmg.PMG_OP_RESIDUAL, 0, U0[r], F[r], r0)
+        relres.append((rr.norm() / r0.norm()).item())
+    for v in res.values():
+        v.pop("u")
+    return {"workload": f"quarter annulus Poisson, h=2^-{k}, p={p}, {BATCHED_NRHS} right-hand sides "
+                        "(f scaled by U[0.5,2] plus 1% nodal noise), 1e-8 relres each",
+            "dofs": N, "nrhs": BATCHED_NRHS, "l2_flush": "2x L2 write before every timed solve",
+            "plain_fp64_single": {"ms_per_solve": 1e3 * t_single, "solves_per_s": world / t_single,
+                                  "MDOF_iter_per_s": world * N * single / t_single / 1e6, "iterations": single},
+            **res,
+            "mixed_vs_plain_fp64_solves_per_s": res["mixed"]["solves_per_s"] * t_single / world,
+            "mixed_vs_batched_fp64_solves_per_s": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"],
+            "mixed_error": {"max_rel_diff_u_vs_fp64": du.max().item(),
+                            "max_final_fp64_relres": max(relres)}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -302,6 +366,8 @@ def run_ours(args):
     t_e2e = reduce_step_time(time.perf_counter() - t0, dist, "cuda")
     e2e_value = job_value(e2e_units, world, t_e2e)
 
+    batched = None if args.no_batched or args.case else _batched_section(args, dist, flush, stream, world)
+
     if rank != 0:
         return
     line = {
@@ -326,6 +392,8 @@ def run_ours(args):
                           "MDOF_iter_per_s_h2^-8": {"p2": 1.02, "p3": 0.76, "p4": 0.56, "p5": 0.41},
                           "note": "paper: benchmark-1 polynomial solution, direct projection"},
     }
+    if batched is not None:
+        line["batched"] = batched
     if world == 1 and not args.no_cpu_baseline and not args.case:
         v, secs, solves = _oracle_sample(args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -343,6 +411,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-right-hand-side section")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -51,16 +51,18 @@ __device__ __forceinline__ float ld_relaxed_t<float>(const float* p) {
   return __uint_as_float(v);
 }
 
-// Bounded poll of a pending value (global or shared memory).
+// Bounded poll of a pending value (global or shared memory).  On expiry the
+// error word gets bit `site` (which wait gave up) and the value reads as 0.
+enum : unsigned { kSiteGlobal = 1u, kSiteShared = 2u, kSiteSlotFree = 4u, kSiteSlotFilled = 8u };
 template <class T, bool SHARED>
-__device__ __forceinline__ T lpb_wait(const T* p, unsigned* err) {
+__device__ __forceinline__ T lpb_wait(const T* p, unsigned* err, unsigned site = SHARED ? kSiteShared : kSiteGlobal) {
   const long long t0 = clock64();
   for (unsigned it = 0;; ++it) {
     const T v = SHARED ? *reinterpret_cast<const volatile T*>(p) : ld_relaxed_t<T>(p);
     if (!Pending<T>::is(v)) return v;
     if (!SHARED) __nanosleep(it < 16 ? 32 : 256);
     if ((it & 31u) == 31u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
-      atomicOr(err, 1u);
+      atomicOr(err, site);
       return T(0);
     }
   }
@@ -169,21 +171,22 @@ __global__ void __launch_bounds__(32 * kLpbMaxLines) k_lpb(LpB<T> M, int R, cons
           jj[q] = t < end ? __ldg(M.ci + t) : -1;
           cv[q] = t < end ? __ldg(M.v + t) : T(0);
         }
+        // rows of this CTA (written by this lane or by another warp) from shared
+        // memory, earlier rows from global memory: issue all loads, then resolve
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int j = jj[q];
-          T v = T(0);
-          if (j >= base_row) {
-            // a row of this CTA: written by this lane (own line, never pending) or by another warp
-            volatile T* p = xs + (size_t)(j - base_row) * 32 + lane;
-            v = *p;
-            if (Pending<T>::is(v)) v = lpb_wait<T, true>(const_cast<const T*>(p), err);
-          } else if (j >= 0) {
-            const T* p = x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col;
-            v = ld_relaxed_t<T>(p);
-            if (Pending<T>::is(v)) v = lpb_wait<T, false>(p, err);
+          xv[q] = T(0);
+          if (j >= base_row) xv[q] = xs[(size_t)(j - base_row) * 32 + lane];
+          else if (j >= 0) xv[q] = ld_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (Pending<T>::is(xv[q])) {
+            const int j = jj[q];
+            xv[q] = j >= base_row ? lpb_wait<T, true>(const_cast<const T*>(xs + (size_t)(j - base_row) * 32 + lane), err)
+                                  : lpb_wait<T, false>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col, err);
           }
-          xv[q] = v;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) a[q & 3] = fma(cv[q], xv[q], a[q & 3]);
@@ -194,6 +197,181 @@ __global__ void __launch_bounds__(32 * kLpbMaxLines) k_lpb(LpB<T> M, int R, cons
       xs[(size_t)(i - base_row) * 32 + lane] = xt;
       st_relaxed_t<T>(x + o, xt);
       if (UPDATE) u[o] += xt;
+    }
+  }
+}
+
+// Line-pipelined lower solve, 32 right-hand sides per item (lane = RHS), with
+// the own-line recurrence split off the critical path (ring width W <= 32):
+//   x_i = s_i - sum_{k=1..W-1} c_{i-k,k} x_{i-k},
+//   s_i = d_i b_i - sum_{far j} d_i M_ij x_j,     c_{j,k} = d_{j+k} M_{j+k,j}
+// (the "ring" entries are those of the row's own line at distance 1..W-1; all
+// others are "far").  One CTA takes one line of one right-hand-side group:
+//  - LpcProducers<T> producer warps compute s_i for rows p, p+P, ... and hand
+//    them over, with the row's ring coefficients, through a 32-slot
+//    shared-memory ring (slot pending = empty);
+//  - one chain warp keeps W running sums per lane in registers (push form:
+//    after x_i is known, every later row of the ring receives c_{i,k} x_i), so
+//    one row costs one subtraction and one FMA on its critical path.
+// Rows of the CTA's own line are read by the producers from shared memory,
+// rows of earlier lines from global memory; both start "pending" (all-ones
+// bits) and every read of a pending value polls, bounded.  Items are claimed
+// in order (line-major), so every item waited for belongs to a running CTA.
+// Producer warps per CTA.  The count must divide 32: hand-over slot k then
+// always belongs to the same producer, which fills it in row order, so a
+// pending (empty) slot unambiguously means that its previous row has been
+// taken by the chain.
+template <class T>
+struct LpcProducers { static constexpr int value = 8; };
+static_assert(32 % LpcProducers<float>::value == 0 && 32 % LpcProducers<double>::value == 0,
+              "producer count must divide the 32 hand-over slots");
+
+template <class T>
+struct LpC {
+  int n, nx, nlines;
+  int ring;           // ring width: own-line entries at distance 1..ring-1 are pushed
+  const int* frp;
+  const int* fci;
+  const T* fv;        // far entries, values scaled by d_i
+  const T* push;      // [n][32]: push[j*32 + k-1] = c_{j,k}
+  const T* dscale;    // d_i, or null when d = 1
+};
+
+// The first NC coefficients of a hand-over row in shared memory (16-byte aligned).
+template <int NC>
+__device__ __forceinline__ void lds_row(const float* p, float (&c)[NC]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int m = 0; m < (NC + 3) / 4; ++m) {
+    const float4 v = q[m];
+    if (4 * m < NC) c[4 * m] = v.x;
+    if (4 * m + 1 < NC) c[4 * m + 1] = v.y;
+    if (4 * m + 2 < NC) c[4 * m + 2] = v.z;
+    if (4 * m + 3 < NC) c[4 * m + 3] = v.w;
+  }
+}
+template <int NC>
+__device__ __forceinline__ void lds_row(const double* p, double (&c)[NC]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int m = 0; m < (NC + 1) / 2; ++m) {
+    const double2 v = q[m];
+    if (2 * m < NC) c[2 * m] = v.x;
+    if (2 * m + 1 < NC) c[2 * m + 1] = v.y;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T lpc_wait_filled(volatile T* p, unsigned* err, unsigned site = kSiteShared) {
+  T v = *p;
+  if (!Pending<T>::is(v)) return v;
+  return lpb_wait<T, true>(const_cast<const T*>(p), err, site);
+}
+
+template <class T, bool MIRROR, int RING>
+__global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T> M, int R, const T* __restrict__ b, T* x,
+                                                                   unsigned* counter, unsigned* err) {
+  static_assert(RING >= 2 && RING <= 32 && (RING & (RING - 1)) == 0, "ring must be a power of two <= 32");
+  constexpr int NC = RING - 1;
+  constexpr int BATCH = sizeof(T) == 4 ? 32 : 16;
+  extern __shared__ __align__(16) unsigned char lpc_smem[];
+  using PU = typename Pending<T>::U;
+  volatile T* xs = reinterpret_cast<volatile T*>(lpc_smem);   // [nx][32] values of the line
+  volatile T* sb = xs + (size_t)M.nx * 32;                    // [32][32] hand-over ring: s_i
+  T* cb = const_cast<T*>(sb) + 32 * 32;                        // [32][32] hand-over ring: c_{i,.}
+  __shared__ int s_item;
+  const int nx = M.nx, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = R >> 5;
+  const int nitems = M.nlines * G;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    for (int t = threadIdx.x; t < (nx + 32) * 32; t += blockDim.x)
+      reinterpret_cast<volatile PU*>(lpc_smem)[t] = Pending<T>::bits;
+    __syncthreads();
+    const int item = s_item;
+    if (item >= nitems) return;
+    const int line = item / G, g = item % G;
+    const int row0 = line * nx, col = g * 32 + lane;
+    if (warp == 0) {
+      T acc[RING];
+#pragma unroll
+      for (int k = 0; k < RING; ++k) acc[k] = T(0);
+      for (int i0 = 0; i0 < nx; i0 += 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int ix = i0 + k;
+          if (ix < nx) {
+            volatile T* slot = sb + k * 32 + lane;
+            const T s = lpc_wait_filled(slot, err, kSiteSlotFilled);
+            __threadfence_block();              // the row's coefficients were written before s
+            T c[NC];
+            lds_row<NC>(cb + k * 32, c);
+            const int a0 = k & (RING - 1);
+            const T xv = s - acc[a0];
+            acc[a0] = T(0);
+#pragma unroll
+            for (int m = 1; m < RING; ++m) acc[(k + m) & (RING - 1)] = fma(c[m - 1], xv, acc[(k + m) & (RING - 1)]);
+            // the pushes consumed c: release the slot to its producer
+            *reinterpret_cast<volatile PU*>(slot) = Pending<T>::bits;
+            xs[(size_t)ix * 32 + lane] = xv;
+            st_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(row0 + ix, M.n) * R + col, xv);
+          }
+        }
+      }
+    } else {
+      const int pw = warp - 1;
+      for (int ix = pw; ix < nx; ix += LpcProducers<T>::value) {
+        const int i = row0 + ix;
+        const size_t o = (size_t)lp_vec<MIRROR>(i, M.n) * R + col;
+        const T bi = M.dscale ? b[o] * __ldg(M.dscale + i) : b[o];
+        const T cf = lane < NC ? __ldg(M.push + (size_t)i * 32 + lane) : T(0);
+        const int beg = __ldg(M.frp + i), end = __ldg(M.frp + i + 1);
+        T a[4] = {T(0), T(0), T(0), T(0)};
+        for (int t0 = beg; t0 < end; t0 += BATCH) {
+          int jj[BATCH];
+          T cv[BATCH], xv[BATCH];
+#pragma unroll
+          for (int q = 0; q < BATCH; ++q) {
+            const int t = t0 + q;
+            jj[q] = t < end ? __ldg(M.fci + t) : -1;
+            cv[q] = t < end ? __ldg(M.fv + t) : T(0);
+          }
+          // Issue every load of the batch first, then resolve the pending ones
+          // (own line from shared memory, earlier lines with relaxed loads at
+          // GPU scope, which read L2: x is written during this kernel).
+#pragma unroll
+          for (int q = 0; q < BATCH; ++q) {
+            const int j = jj[q];
+            xv[q] = T(0);
+            if (j >= row0) xv[q] = xs[(size_t)(j - row0) * 32 + lane];
+            else if (j >= 0) xv[q] = ld_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col);
+          }
+#pragma unroll
+          for (int q = 0; q < BATCH; ++q) {
+            if (Pending<T>::is(xv[q])) {
+              const int j = jj[q];
+              xv[q] = j >= row0 ? lpc_wait_filled(xs + (size_t)(j - row0) * 32 + lane, err)
+                                : lpb_wait<T, false>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col, err);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < BATCH; ++q) a[q & 3] = fma(cv[q], xv[q], a[q & 3]);
+        }
+        const T s = bi - ((a[0] + a[1]) + (a[2] + a[3]));
+        volatile T* slot = sb + (ix & 31) * 32 + lane;
+        // wait for the chain to have taken row ix - 32 out of this slot (bounded)
+        const long long t0 = clock64();
+        for (unsigned it = 0; !Pending<T>::is(*slot); ++it) {
+          if ((it & 31u) == 31u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
+            atomicOr(err, kSiteSlotFree);
+            break;
+          }
+        }
+        cb[(ix & 31) * 32 + lane] = cf;
+        __threadfence_block();                  // coefficients before s
+        *slot = s;
+      }
     }
   }
 }

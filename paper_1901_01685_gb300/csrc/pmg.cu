@@ -8,10 +8,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pmg.h"
@@ -106,6 +108,8 @@ struct DevPLevel {
   pmgk::TCsr<float> A32{}, Res32{}, Pro32{};
   pmgk::LpB<double> Lb64{}, Ub64{};
   pmgk::LpB<float> Lb32{}, Ub32{};
+  pmgk::LpC<double> Lc64{}, Uc64{};   // ring kernel layouts (U mirrored)
+  pmgk::LpC<float> Lc32{}, Uc32{};
 };
 struct DevHLevel {
   int N = 0, ne = 0;
@@ -115,6 +119,7 @@ struct DevHLevel {
   pmgk::Lp2 Lolp{}, UpMlp{};
   double avg_lo = 0, avg_up = 0;
   pmgk::LpB<double> Lob{}, UpMb{};   // batched Gauss-Seidel layouts
+  pmgk::LpC<double> Loc{}, UpMc{};
 };
 
 }  // namespace
@@ -133,6 +138,10 @@ struct pmg_hierarchy_s {
   std::vector<BOff> boff;
   struct HBOff { DevCsrOff UpM; size_t dinvM; };
   std::vector<HBOff> hboff;
+  // ring kernel layouts: far parts (FP64 CSR + FP32 values), FP32 push rings and scales
+  std::vector<pmgl::Csr> farstore;
+  struct COff { DevCsrOff far; int ring; size_t far32, push32, d32; };
+  std::vector<COff> coffL, coffU, coffL32, coffU32, coffLo, coffUpM;
   size_t off_cinv = 0;
   bool uploaded = false;
   char* arena = nullptr;
@@ -536,7 +545,9 @@ pmg_status finish_launches(Ctx& c) {
   collect_profile(c.w);
   if (err) {
     cudaMemsetAsync(c.w->err, 0, sizeof(unsigned), c.s);
-    return fail(PMG_ERR_TIMEOUT, "a device-side dependency wait expired");
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "a device-side dependency wait expired (wait sites 0x%x)", err);
+    return fail(PMG_ERR_TIMEOUT, buf);
   }
   return PMG_OK;
 }
@@ -619,6 +630,53 @@ void b_lp(Ctx& c, int cls, const pmgk::LpB<T>& M, long long nnz, bool mirror, co
   });
 }
 
+// Ring-kernel batched solve; false when the line does not fit in shared memory.
+template <class T>
+bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x) {
+  const size_t smem = size_t(M.nx + 64) * 32 * sizeof(T);
+  if (smem > kLpSmemCap) return false;
+  const int R = c.w->R, threads = 32 * (1 + pmgk::LpcProducers<T>::value);
+  const void* fn = nullptr;
+  auto pick = [&](auto mir, auto ring) {
+    fn = (const void*)pmgk::k_lpc<T, decltype(mir)::value, decltype(ring)::value>;
+  };
+  using F_ = std::false_type;
+  using T_ = std::true_type;
+  using R2 = std::integral_constant<int, 2>;
+  using R16 = std::integral_constant<int, 16>;
+  using R32 = std::integral_constant<int, 32>;
+  switch (M.ring) {
+    case 2: mirror ? pick(T_{}, R2{}) : pick(F_{}, R2{}); break;
+    case 16: mirror ? pick(T_{}, R16{}) : pick(F_{}, R16{}); break;
+    case 32:
+      if constexpr (sizeof(T) == 4) { mirror ? pick(T_{}, R32{}) : pick(F_{}, R32{}); break; }
+      return false;   // FP64 chains use narrower rings
+    default: return false;
+  }
+  allow_smem(fn);
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+  const int nitems = M.nlines * (R / 32);
+  const int grid = std::max(1, std::min(nitems, c.h->sms * occ));
+  unsigned* cnt = next_counter(c);
+  launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
+    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
+    pmgk::LpC<T> m = M;
+    int r = R;
+    const T* bb = b;
+    void* args[] = {&m, &r, &bb, &x, &cnt, &c.w->err};
+    cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, c.s);
+  });
+  return true;
+}
+
+template <class T>
+void b_axpy(Ctx& c, int cls, long long n, const T* x, T* y) {
+  launch(c, cls, 3.0 * n * sizeof(T), [&] {
+    pmgk::k_axpy<T><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
+  });
+}
+
 template <class TI, class TO>
 void b_cast(Ctx& c, long long n, const TI* x, TO* y) {
   pmgk::k_cast<TI, TO><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
@@ -633,7 +691,8 @@ void b_gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   double* xn = c.w->bhg[j];
   if (backward) b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Lo), D.nnzA / 2, x, b, t);
   else b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Up), D.nnzA / 2, x, b, t);
-  b_lp<double>(c, PMG_K_GS, backward ? D.UpMb : D.Lob, D.nnzA / 2, backward, t, xn, nullptr);
+  if (!b_lpc<double>(c, PMG_K_GS, backward ? D.UpMc : D.Loc, D.nnzA / 2, backward, t, xn))
+    b_lp<double>(c, PMG_K_GS, backward ? D.UpMb : D.Lob, D.nnzA / 2, backward, t, xn, nullptr);
   cudaMemcpyAsync(x, xn, size_t(D.N) * R * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
 }
 
@@ -676,6 +735,12 @@ void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
   const pmgk::LpB<T>& Ub = [&]() -> const pmgk::LpB<T>& {
     if constexpr (sizeof(T) == 4) return D.Ub32; else return D.Ub64;
   }();
+  const pmgk::LpC<T>& Lc = [&]() -> const pmgk::LpC<T>& {
+    if constexpr (sizeof(T) == 4) return D.Lc32; else return D.Lc64;
+  }();
+  const pmgk::LpC<T>& Uc = [&]() -> const pmgk::LpC<T>& {
+    if constexpr (sizeof(T) == 4) return D.Uc32; else return D.Uc64;
+  }();
   const pmgk::TCsr<T> Res = [&] {
     if constexpr (sizeof(T) == 4) return D.Res32; else return as_t(D.Res);
   }();
@@ -690,8 +755,9 @@ void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
   auto smooth = [&](bool first) {
     const T* rr = f;
     if (!first) { b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r); rr = r; }
-    b_lp<T>(c, PMG_K_LSOLVE, Lb, D.nnzL, false, rr, y, nullptr);
-    b_lp<T>(c, PMG_K_USOLVE, Ub, D.nnzU, true, y, t, e);
+    if (!b_lpc<T>(c, PMG_K_LSOLVE, Lc, D.nnzL, false, rr, y)) b_lp<T>(c, PMG_K_LSOLVE, Lb, D.nnzL, false, rr, y, nullptr);
+    if (b_lpc<T>(c, PMG_K_USOLVE, Uc, D.nnzU, true, y, t)) b_axpy<T>(c, PMG_K_USOLVE, (long long)D.N * R, t, e);
+    else b_lp<T>(c, PMG_K_USOLVE, Ub, D.nnzU, true, y, t, e);
   };
   for (int m = 0; m < H.opt.nu_pre; ++m) smooth(m == 0);
   b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r);
@@ -881,6 +947,30 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     b.dinvM = P.add(Hl.UpMlp.dscale.data(), Hl.UpMlp.dscale.size() * sizeof(double));
     h->hboff.push_back(b);
   }
+  // Ring widths: FP32 chains push 31 values a row (one FMA each, cheap);
+  // FP64 FMAs are slow on this part, so FP64 ILUT chains push 15 and the P1
+  // sweeps (own-line entries at distance 1 only) push 1.
+  h->farstore.reserve(6 * (h->H.lev.size() + h->H.hl.size()));
+  h->f32store.reserve(h->f32store.size() + 6 * h->H.lev.size());
+  auto plan_ring = [&](const pmgl::Csr& M, const pmgl::LpLayout& lp, int nx, int ring, bool fp32) {
+    h->farstore.push_back(pmgl::far_part(M, nx, lp.dscale, ring));
+    const auto& F = h->farstore.back();
+    pmg_hierarchy_s::COff c{};
+    c.far = plan_csr(P, F);
+    c.ring = ring;
+    if (fp32) { c.far32 = f32(F.v); c.push32 = f32(lp.push); c.d32 = f32(lp.dscale); }
+    return c;
+  };
+  for (const auto& L : h->H.lev) {
+    h->coffL.push_back(plan_ring(L.L, L.Llp, L.n1d, 16, false));
+    h->coffU.push_back(plan_ring(L.Um, L.Ulp, L.n1d, 16, false));
+    h->coffL32.push_back(plan_ring(L.L, L.Llp, L.n1d, 32, true));
+    h->coffU32.push_back(plan_ring(L.Um, L.Ulp, L.n1d, 32, true));
+  }
+  for (const auto& Hl : h->H.hl) {
+    h->coffLo.push_back(plan_ring(Hl.Lo, Hl.Lolp, Hl.n1d, 2, false));
+    h->coffUpM.push_back(plan_ring(Hl.UpM, Hl.UpMlp, Hl.n1d, 2, false));
+  }
   *out = h;
   return PMG_OK;
 }
@@ -986,6 +1076,18 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
                                  reinterpret_cast<const double*>(base + b.udm64)};
       D.Lb32 = pmgk::LpB<float>{D.N, nx, D.N / nx, D.L.rp, D.L.ci, fp(b.L32), nullptr};
       D.Ub32 = pmgk::LpB<float>{D.N, nx, D.N / nx, Um.rp, Um.ci, fp(b.Um32), fp(b.udm32)};
+      const auto& cl = h->coffL[l];
+      const auto& cu = h->coffU[l];
+      const auto& cl32 = h->coffL32[l];
+      const auto& cu32 = h->coffU32[l];
+      const pmgk::Csr FL = bind(cl.far, base), FU = bind(cu.far, base);
+      const pmgk::Csr FL32 = bind(cl32.far, base), FU32 = bind(cu32.far, base);
+      D.Lc64 = pmgk::LpC<double>{D.N, nx, D.N / nx, cl.ring, FL.rp, FL.ci, FL.v, D.Llp.push, nullptr};
+      D.Uc64 = pmgk::LpC<double>{D.N, nx, D.N / nx, cu.ring, FU.rp, FU.ci, FU.v, D.Ulp.push, D.Ulp.dscale};
+      D.Lc32 = pmgk::LpC<float>{D.N, nx, D.N / nx, cl32.ring, FL32.rp, FL32.ci, fp(cl32.far32), fp(cl32.push32),
+                                nullptr};
+      D.Uc32 = pmgk::LpC<float>{D.N, nx, D.N / nx, cu32.ring, FU32.rp, FU32.ci, fp(cu32.far32), fp(cu32.push32),
+                                fp(cu32.d32)};
     }
     h->dl.push_back(D);
   }
@@ -1006,6 +1108,11 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
       D.Lob = pmgk::LpB<double>{D.N, nx, D.N / nx, D.Lo.rp, D.Lo.ci, D.Lo.v, D.dinv};
       D.UpMb = pmgk::LpB<double>{D.N, nx, D.N / nx, UpM.rp, UpM.ci, UpM.v,
                                  reinterpret_cast<const double*>(base + h->hboff[j].dinvM)};
+      const pmgk::Csr FLo = bind(h->coffLo[j].far, base), FUp = bind(h->coffUpM[j].far, base);
+      D.Loc = pmgk::LpC<double>{D.N, nx, D.N / nx, h->coffLo[j].ring, FLo.rp, FLo.ci, FLo.v, D.Lolp.push,
+                                D.Lolp.dscale};
+      D.UpMc = pmgk::LpC<double>{D.N, nx, D.N / nx, h->coffUpM[j].ring, FUp.rp, FUp.ci, FUp.v, D.UpMlp.push,
+                                 D.UpMlp.dscale};
     }
     D.avg_lo = double(h->off_Lo[j].nnz) / std::max(1, D.N);
     D.avg_up = double(h->off_Up[j].nnz) / std::max(1, D.N);

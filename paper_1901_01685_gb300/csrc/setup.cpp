@@ -785,6 +785,23 @@ LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int win
   return P;
 }
 
+Csr far_part(const Csr& M, int nx, const std::vector<double>& dscale, int ring) {
+  Csr F;
+  F.nr = F.nc = M.nr;
+  F.rp.assign(size_t(M.nr) + 1, 0);
+  for (int i = 0; i < M.nr; ++i) {
+    const int line_start = (i / nx) * nx;
+    for (int t = M.rp[i]; t < M.rp[i + 1]; ++t) {
+      const int j = M.ci[t];
+      if (j >= line_start && i - j < ring) continue;
+      F.ci.push_back(j);
+      F.v.push_back(M.v[t] * dscale[size_t(i)]);
+    }
+    F.rp[size_t(i) + 1] = int(F.ci.size());
+  }
+  return F;
+}
+
 int critical_path(const Csr& T, bool lower) {
   const int n = T.nr;
   std::vector<int> lvl(size_t(n), 0);

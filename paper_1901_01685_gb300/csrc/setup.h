@@ -43,6 +43,11 @@ struct LpLayout {
 };
 LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int window_rows, int lanes_per_row);
 
+// Far part of a strict-lower solve for the batched ring kernel: every entry
+// of M except those of the row's own line at distance 1..ring-1 (which the
+// ring of LpLayout::push carries), values scaled by dscale[i].
+Csr far_part(const Csr& M, int nx, const std::vector<double>& dscale, int ring);
+
 // One ILUT-smoothed level of degree q >= 2.
 struct PLevel {
   int q = 0, n1d = 0, N = 0;
