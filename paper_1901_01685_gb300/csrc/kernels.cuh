@@ -529,8 +529,11 @@ __global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
           const int ia = ix + kLpAhead;
           if (ia < nx && lane == (ia & 31)) acc += lp_get_shared<false>(cs_line + ia, err);
           if (lane == 0) {
-            xs_line[ix] = xi;
-            x[lp_vec<MIRROR>(row0 + ix, M.n)] = xi;
+            // a NaN must never read as the pending marker
+            const double xo = (unsigned long long)__double_as_longlong(xi) == kPending
+                                  ? __longlong_as_double(0x7FF8000000000000ll) : xi;
+            xs_line[ix] = xo;
+            x[lp_vec<MIRROR>(row0 + ix, M.n)] = xo;
           }
         }
       }

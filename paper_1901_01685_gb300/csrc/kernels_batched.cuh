@@ -28,12 +28,14 @@ struct Pending<double> {
   using U = unsigned long long;
   static constexpr U bits = 0xFFFFFFFFFFFFFFFFull;
   __device__ static bool is(double v) { return (U)__double_as_longlong(v) == bits; }
+  __device__ static double other_nan() { return __longlong_as_double(0x7FF8000000000000ll); }
 };
 template <>
 struct Pending<float> {
   using U = unsigned int;
   static constexpr U bits = 0xFFFFFFFFu;
   __device__ static bool is(float v) { return (U)__float_as_uint(v) == bits; }
+  __device__ static float other_nan() { return __uint_as_float(0x7FC00000u); }
 };
 
 template <class T>
@@ -54,15 +56,28 @@ __device__ __forceinline__ float ld_relaxed_t<float>(const float* p) {
 // Bounded poll of a pending value (global or shared memory).  On expiry the
 // error word gets bit `site` (which wait gave up) and the value reads as 0.
 enum : unsigned { kSiteGlobal = 1u, kSiteShared = 2u, kSiteSlotFree = 4u, kSiteSlotFilled = 8u };
+// err[0] collects the bits of every wait that gave up; the first one to give
+// up also records (site, work item, row, warp) in err[1..3].
+__device__ __forceinline__ void wait_expired(unsigned* err, unsigned site, int item, int row) {
+  if (atomicCAS(err + 1, 0u, site) == 0u) {
+    err[2] = (unsigned)item;
+    err[3] = ((unsigned)row << 8) | (threadIdx.x >> 5);
+  }
+  atomicOr(err, site);
+}
+
 template <class T, bool SHARED>
-__device__ __forceinline__ T lpb_wait(const T* p, unsigned* err, unsigned site = SHARED ? kSiteShared : kSiteGlobal) {
+__device__ __forceinline__ T lpb_wait(const T* p, unsigned* err, unsigned site = SHARED ? kSiteShared : kSiteGlobal,
+                                      int item = -1, int row = -1) {
   const long long t0 = clock64();
   for (unsigned it = 0;; ++it) {
     const T v = SHARED ? *reinterpret_cast<const volatile T*>(p) : ld_relaxed_t<T>(p);
     if (!Pending<T>::is(v)) return v;
-    if (!SHARED) __nanosleep(it < 16 ? 32 : 256);
+    // Global waits back off (32 ns for 16 polls, then 256 ns); longer or
+    // exponential back-off measured slower on the pipeline front.
+    if (!SHARED) __nanosleep(it < 16 ? 32u : 256u);
     if ((it & 31u) == 31u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
-      atomicOr(err, site);
+      wait_expired(err, site, item, row);
       return T(0);
     }
   }
@@ -194,6 +209,7 @@ __global__ void __launch_bounds__(32 * kLpbMaxLines) k_lpb(LpB<T> M, int R, cons
       const size_t o = (size_t)lp_vec<MIRROR>(i, M.n) * R + col;
       T xt = b[o] - ((a[0] + a[1]) + (a[2] + a[3]));
       if (M.dscale) xt *= __ldg(M.dscale + i);
+      if (Pending<T>::is(xt)) xt = Pending<T>::other_nan();   // never publish the marker
       xs[(size_t)(i - base_row) * 32 + lane] = xt;
       st_relaxed_t<T>(x + o, xt);
       if (UPDATE) u[o] += xt;
@@ -262,10 +278,10 @@ __device__ __forceinline__ void lds_row(const double* p, double (&c)[NC]) {
 }
 
 template <class T>
-__device__ __forceinline__ T lpc_wait_filled(volatile T* p, unsigned* err, unsigned site = kSiteShared) {
+__device__ __forceinline__ T lpc_wait_filled(volatile T* p, unsigned* err, unsigned site, int item, int row) {
   T v = *p;
   if (!Pending<T>::is(v)) return v;
-  return lpb_wait<T, true>(const_cast<const T*>(p), err, site);
+  return lpb_wait<T, true>(const_cast<const T*>(p), err, site, item, row);
 }
 
 template <class T, bool MIRROR, int RING>
@@ -303,12 +319,13 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
           const int ix = i0 + k;
           if (ix < nx) {
             volatile T* slot = sb + k * 32 + lane;
-            const T s = lpc_wait_filled(slot, err, kSiteSlotFilled);
+            const T s = lpc_wait_filled(slot, err, kSiteSlotFilled, item, ix);
             __threadfence_block();              // the row's coefficients were written before s
             T c[NC];
             lds_row<NC>(cb + k * 32, c);
             const int a0 = k & (RING - 1);
-            const T xv = s - acc[a0];
+            T xv = s - acc[a0];
+            if (Pending<T>::is(xv)) xv = Pending<T>::other_nan();   // never publish the marker
             acc[a0] = T(0);
 #pragma unroll
             for (int m = 1; m < RING; ++m) acc[(k + m) & (RING - 1)] = fma(c[m - 1], xv, acc[(k + m) & (RING - 1)]);
@@ -351,8 +368,9 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
           for (int q = 0; q < BATCH; ++q) {
             if (Pending<T>::is(xv[q])) {
               const int j = jj[q];
-              xv[q] = j >= row0 ? lpc_wait_filled(xs + (size_t)(j - row0) * 32 + lane, err)
-                                : lpb_wait<T, false>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col, err);
+              xv[q] = j >= row0 ? lpc_wait_filled(xs + (size_t)(j - row0) * 32 + lane, err, kSiteShared, item, ix)
+                                : lpb_wait<T, false>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col, err,
+                                                     kSiteGlobal, item, ix);
             }
           }
 #pragma unroll
@@ -364,12 +382,19 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
         const long long t0 = clock64();
         for (unsigned it = 0; !Pending<T>::is(*slot); ++it) {
           if ((it & 31u) == 31u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
-            atomicOr(err, kSiteSlotFree);
+            wait_expired(err, kSiteSlotFree, item, ix);
             break;
           }
         }
+        // The chain's lane L reads the coefficients of all lanes but waits
+        // only for slot lane L, so the warp converges twice: every lane's slot
+        // has been released (row ix - 32 fully consumed) before any lane
+        // overwrites the row's coefficients, and every coefficient is written
+        // before any lane publishes s.
+        __syncwarp();
         cb[(ix & 31) * 32 + lane] = cf;
-        __threadfence_block();                  // coefficients before s
+        __syncwarp();
+        __threadfence_block();
         *slot = s;
       }
     }

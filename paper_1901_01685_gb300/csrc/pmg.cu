@@ -241,7 +241,7 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
   for (const auto& Hl : H.hl) maxLines = std::max(maxLines, Hl.N / std::max(1, Hl.n1d));
   W.lprog = take(size_t(maxLines) * sizeof(unsigned long long));
   W.counters = take(kCounterSlots * sizeof(unsigned));
-  W.err = take(sizeof(unsigned));
+  W.err = take(4 * sizeof(unsigned));
   W.partial = take(pmgk::kNormBlocks * sizeof(double));
   W.r0 = take(sizeof(double));
   W.hist = take(kHistCap * sizeof(double));
@@ -539,14 +539,17 @@ pmg_status begin_launches(Ctx& c) {
 
 pmg_status finish_launches(Ctx& c) {
   PMG_CUDA(cudaGetLastError());
-  unsigned err = 0;
-  PMG_CUDA(cudaMemcpyAsync(&err, c.w->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
+  unsigned errw[4] = {0, 0, 0, 0};
+  PMG_CUDA(cudaMemcpyAsync(errw, c.w->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
+  const unsigned err = errw[0];
   PMG_CUDA(cudaStreamSynchronize(c.s));
   collect_profile(c.w);
   if (err) {
-    cudaMemsetAsync(c.w->err, 0, sizeof(unsigned), c.s);
-    char buf[96];
-    std::snprintf(buf, sizeof(buf), "a device-side dependency wait expired (wait sites 0x%x)", err);
+    cudaMemsetAsync(c.w->err, 0, 4 * sizeof(unsigned), c.s);
+    char buf[160];
+    std::snprintf(buf, sizeof(buf),
+                  "a device-side dependency wait expired (wait sites 0x%x; first: site 0x%x, item %u, row %u, warp %u)",
+                  err, errw[1], errw[2], errw[3] >> 8, errw[3] & 0xffu);
     return fail(PMG_ERR_TIMEOUT, buf);
   }
   return PMG_OK;
