@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(32 * kLpbMaxLines) k_lpb(LpB<T> M, int R, cons
   }
 }
 
-// Line-pipelined lower solve, 32 right-hand sides per item (lane = RHS), with
+// Line-pipelined lower solve, 32 right-hand sides per item (lane = RHS; or
+// one vector when R == 1), with
 // the own-line recurrence split off the critical path (ring width W <= 32):
 //   x_i = s_i - sum_{k=1..W-1} c_{i-k,k} x_{i-k},
 //   s_i = d_i b_i - sum_{far j} d_i M_ij x_j,     c_{j,k} = d_{j+k} M_{j+k,j}
@@ -297,7 +298,10 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
   T* cb = const_cast<T*>(sb) + 32 * 32;                        // [32][32] hand-over ring: c_{i,.}
   __shared__ int s_item;
   const int nx = M.nx, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int G = R >> 5;
+  // R == 1: one plain vector, every lane computes the same values (loads are
+  // broadcasts, stores coincide)
+  const bool single = R == 1;
+  const int G = single ? 1 : R >> 5;
   const int nitems = M.nlines * G;
   for (;;) {
     __syncthreads();
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
     const int item = s_item;
     if (item >= nitems) return;
     const int line = item / G, g = item % G;
-    const int row0 = line * nx, col = g * 32 + lane;
+    const int row0 = line * nx, col = single ? 0 : g * 32 + lane;
     if (warp == 0) {
       T acc[RING];
 #pragma unroll

@@ -412,11 +412,61 @@ void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
 // forward  (D + L) x_new = b - U x_old,  backward  (D + U) x_new = b - L x_old.
 // The new values go to a scratch vector first (the solve polls its output for
 // readiness, so it cannot overwrite x in place) and are copied back.
+// Ring-kernel batched solve; false when the line does not fit in shared memory.
+template <class T>
+bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0) {
+  const size_t smem = size_t(M.nx + 64) * 32 * sizeof(T);
+  if (smem > kLpSmemCap) return false;
+  const int R = nrhs > 0 ? nrhs : c.w->R, threads = 32 * (1 + pmgk::LpcProducers<T>::value);
+  const void* fn = nullptr;
+  auto pick = [&](auto mir, auto ring) {
+    fn = (const void*)pmgk::k_lpc<T, decltype(mir)::value, decltype(ring)::value>;
+  };
+  using F_ = std::false_type;
+  using T_ = std::true_type;
+  using R2 = std::integral_constant<int, 2>;
+  using R16 = std::integral_constant<int, 16>;
+  using R32 = std::integral_constant<int, 32>;
+  switch (M.ring) {
+    case 2: mirror ? pick(T_{}, R2{}) : pick(F_{}, R2{}); break;
+    case 16: mirror ? pick(T_{}, R16{}) : pick(F_{}, R16{}); break;
+    case 32:
+      if constexpr (sizeof(T) == 4) { mirror ? pick(T_{}, R32{}) : pick(F_{}, R32{}); break; }
+      return false;   // FP64 chains use narrower rings
+    default: return false;
+  }
+  allow_smem(fn);
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+  const int nitems = M.nlines * std::max(1, R / 32);
+  const int grid = std::max(1, std::min(nitems, c.h->sms * occ));
+  unsigned* cnt = next_counter(c);
+  launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
+    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
+    pmgk::LpC<T> m = M;
+    int r = R;
+    const T* bb = b;
+    void* args[] = {&m, &r, &bb, &x, &cnt, &c.w->err};
+    cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, c.s);
+  });
+  return true;
+}
+
 void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   const DevHLevel& D = c.h->dh[j];
   double* t = c.w->hr[j];
   double* xn = c.w->hg[j];
   const pmgk::Csr& other = backward ? D.Lo : D.Up;
+  // the ring kernel in its one-vector form: the old-value part as an SpMV, the
+  // new values by the line-pipelined solve with a 2-wide ring
+  const pmgk::LpC<double>& ring = backward ? D.UpMc : D.Loc;
+  if (size_t(ring.nx + 64) * 32 * sizeof(double) <= kLpSmemCap) {
+    launch(c, PMG_K_GS, csr_bytes(D.nnzA / 2, D.N) + 24.0 * D.N,
+           [&] { spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms); });
+    b_lpc<double>(c, PMG_K_GS, ring, D.nnzA / 2, backward, t, xn, 1);
+    cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+    return;
+  }
   launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
     spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms);
     if (lp_launch(c, backward ? D.UpMlp : D.Lolp, backward, t, xn, nullptr)) {
@@ -631,46 +681,6 @@ void b_lp(Ctx& c, int cls, const pmgk::LpB<T>& M, long long nnz, bool mirror, co
     if (k == 2) { allow_smem((const void*)pmgk::k_lpb<T, true, false>); pmgk::k_lpb<T, true, false><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
     if (k == 3) { allow_smem((const void*)pmgk::k_lpb<T, true, true>); pmgk::k_lpb<T, true, true><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
   });
-}
-
-// Ring-kernel batched solve; false when the line does not fit in shared memory.
-template <class T>
-bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x) {
-  const size_t smem = size_t(M.nx + 64) * 32 * sizeof(T);
-  if (smem > kLpSmemCap) return false;
-  const int R = c.w->R, threads = 32 * (1 + pmgk::LpcProducers<T>::value);
-  const void* fn = nullptr;
-  auto pick = [&](auto mir, auto ring) {
-    fn = (const void*)pmgk::k_lpc<T, decltype(mir)::value, decltype(ring)::value>;
-  };
-  using F_ = std::false_type;
-  using T_ = std::true_type;
-  using R2 = std::integral_constant<int, 2>;
-  using R16 = std::integral_constant<int, 16>;
-  using R32 = std::integral_constant<int, 32>;
-  switch (M.ring) {
-    case 2: mirror ? pick(T_{}, R2{}) : pick(F_{}, R2{}); break;
-    case 16: mirror ? pick(T_{}, R16{}) : pick(F_{}, R16{}); break;
-    case 32:
-      if constexpr (sizeof(T) == 4) { mirror ? pick(T_{}, R32{}) : pick(F_{}, R32{}); break; }
-      return false;   // FP64 chains use narrower rings
-    default: return false;
-  }
-  allow_smem(fn);
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
-  const int nitems = M.nlines * (R / 32);
-  const int grid = std::max(1, std::min(nitems, c.h->sms * occ));
-  unsigned* cnt = next_counter(c);
-  launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
-    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
-    pmgk::LpC<T> m = M;
-    int r = R;
-    const T* bb = b;
-    void* args[] = {&m, &r, &bb, &x, &cnt, &c.w->err};
-    cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, c.s);
-  });
-  return true;
 }
 
 template <class T>

@@ -168,3 +168,22 @@ def test_batched_full_size_annulus(torch_mod, pmg, oracle_mod, p):
         assert np.linalg.norm(Un[r] - uo) <= U_TOL * np.linalg.norm(uo)
         assert _relres(O, F[r], Umn[r], U0[r]) < RELRES_SLACK
         assert itm[r] <= ito + 2
+
+
+def test_batched_repeated_solves_are_bit_identical(torch_mod, pmg, oracle_mod):
+    """Every value of a batched solve is computed by one lane in a fixed order,
+    so repeating the solve reproduces it bit for bit; a race in the pipelined
+    solves (a value read before it is final) shows up here as a difference."""
+    torch = torch_mod
+    S = pmg.Solver(0, 5, 7, max_rhs=64)
+    f = S.rhs()
+    F = inputs.batched_rhs(f, 64, seed=21)
+    U0 = np.stack([inputs.initial_guess(S.N, 200 + r) for r in range(64)])
+    Fd, U0d = _dev(torch, F), _dev(torch, U0)
+    for prec in (pmg.PMG_PREC_FP64, pmg.PMG_PREC_MIXED):
+        ref, it0, h0, _ = S.solve_batched(Fd, U0d, precision=prec)
+        ref = ref.clone()
+        for _ in range(3):
+            U, it, h, st = S.solve_batched(Fd, U0d, precision=prec)
+            assert st == 0 and np.array_equal(it, it0) and np.array_equal(h, h0)
+            assert torch.equal(U, ref)
