@@ -201,6 +201,8 @@ def _batched_section(args, dist, flush, stream, world):
 
     dom, p, k = BATCHED_CASE
     S = pmg.Solver(dom, p, k, max_rhs=BATCHED_NRHS)
+    if not args.no_autotune:
+        S.autotune()
     N = S.N
     F = torch.as_tensor(inputs.batched_rhs(S.rhs(), BATCHED_NRHS, seed=2), device="cuda")
     U0 = torch.as_tensor(np.stack([inputs.initial_guess(N, 1)] * BATCHED_NRHS), device="cuda")
@@ -243,6 +245,7 @@ def _batched_section(args, dist, flush, stream, world):
     return {"workload": f"quarter annulus Poisson, h=2^-{k}, p={p}, {BATCHED_NRHS} right-hand sides "
                         "(f scaled by U[0.5,2] plus 1% nodal noise), 1e-8 relres each",
             "dofs": N, "nrhs": BATCHED_NRHS, "l2_flush": "2x L2 write before every timed solve",
+            "kernels": {"levels": S.info["kernels_p"], "p1_levels": S.info["kernels_h"]},
             "plain_fp64_single": {"ms_per_solve": 1e3 * t_single, "solves_per_s": world / t_single,
                                   "MDOF_iter_per_s": world * N * single / t_single / 1e6, "iterations": single},
             **res,
@@ -282,6 +285,8 @@ def run_ours(args):
     solvers, fdev, u0dev, udev = [], [], [], []
     for dom, p, k in cases:
         S = pmg.Solver(dom, p, k)
+        if not args.no_autotune:
+            S.autotune()            # kernel variant per solve, measured on this GPU (setup, untimed)
         solvers.append(S)
         fdev.append(torch.as_tensor(S.rhs(), device="cuda"))
         u0dev.append(torch.as_tensor(inputs.initial_guess(S.N, 1), device="cuda"))
@@ -376,6 +381,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload, "cases": cases, "dofs": [S.N for S in solvers],
                    "iterations": iters, "parallelism": f"replicas{world}", "l2_flush": "2x L2 write between steps",
+                   "kernels": [{"p": S.info["p"], "levels": S.info["kernels_p"], "p1_levels": S.info["kernels_h"]}
+                               for S in solvers],
                    "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(dom),
@@ -412,6 +419,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-right-hand-side section")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()
     if args.impl == "reference":

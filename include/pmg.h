@@ -94,6 +94,13 @@ typedef struct {
   double setup_ms_assembly, setup_ms_ilut, setup_ms_transfer, setup_ms_hmg;
   double cycle_bytes;                   /* algorithmic DRAM bytes of one V-cycle */
   double cycle_flops;                   /* floating-point operations of one V-cycle */
+  /* kernel variant of each solve (0 windowed line-pipelined, 1 ring, 2 lines
+   * per CTA), two bits each.  tune_p[l]: single-vector forward, backward;
+   * batched FP64 forward, backward; batched FP32 forward, backward.
+   * tune_h[j]: single-vector forward, backward sweep; batched forward,
+   * backward sweep. */
+  int tune_p[PMG_MAX_LEVELS];
+  int tune_h[PMG_MAX_LEVELS];
 } pmg_info_t;
 
 typedef struct pmg_hierarchy_s* pmg_handle;
@@ -171,6 +178,24 @@ enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1 };
 pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F_dev, const double* U0_dev,
                              double rel_tol, int max_iter, int precision, double* U_dev, int* iters_host,
                              double* hist_host, void* stream);
+
+/* Kernel autotuner (the paper has no counterpart): times every available
+ * kernel variant of each triangular solve and Gauss-Seidel sweep of the
+ * hierarchy on the current device, single-vector and (if the workspace holds
+ * several right-hand sides) batched in both precisions, with the workspace's
+ * buffers as scratch, and keeps the fastest for later solves on this handle.
+ * The variants compute the same operation with a different order of
+ * floating-point summation.  Blocks until done.  Not to be called while
+ * another solve uses the handle.  Errors: PMG_ERR_ARG, PMG_ERR_STATE,
+ * PMG_ERR_TIMEOUT, PMG_ERR_CUDA. */
+pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream);
+
+/* Sets the kernel variant of every solve by hand, in the packing of
+ * pmg_info_t.tune_p / tune_h (arrays of nlevels / nhlevels ints): single-vector
+ * solves and sweeps take 0 or 1, batched ones 1 or 2.  The hierarchy must be
+ * uploaded.  Errors: PMG_ERR_ARG (a variant out of range; nothing changed),
+ * PMG_ERR_STATE. */
+pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h);
 
 /* Single steps of the cycle, for checking each one on its own.  `level` is a
  * p-level index (0 = degree p) for the first group and a P1 level index

@@ -529,6 +529,11 @@ __global__ void k_masked_update(long long n, int R, const TI* __restrict__ e, co
     u[t] += mask[t % R] * (double)e[t];
 }
 template <class T>
+__global__ void k_fill(long long total, T v, T* __restrict__ y) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+    y[t] = v;
+}
+template <class T>
 __global__ void k_axpy(long long total, const T* __restrict__ x, T* __restrict__ y) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
     y[t] += x[t];

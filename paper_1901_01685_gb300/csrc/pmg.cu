@@ -111,6 +111,20 @@ struct DevPLevel {
   pmgk::LpC<double> Lc64{}, Uc64{};   // ring kernel layouts (U mirrored)
   pmgk::LpC<float> Lc32{}, Uc32{};
 };
+// Kernel variant of each solve: the line-pipelined windowed kernel (single
+// vectors), the ring kernel, or the lines-per-CTA kernel (batched).  Defaults
+// are the measured best on GB300; pmg_autotune re-measures them.
+enum : unsigned char { kVarLp2 = 0, kVarRing = 1, kVarLines = 2 };
+struct PTune {
+  unsigned char sL = kVarLp2, sU = kVarLp2;           // single vector: forward / backward ILUT solve
+  unsigned char bL[2] = {kVarRing, kVarRing};         // batched, [0] FP64, [1] FP32
+  unsigned char bU[2] = {kVarRing, kVarRing};
+};
+struct HTune {
+  unsigned char gF = kVarRing, gB = kVarRing;         // single vector: forward / backward sweep
+  unsigned char bF = kVarRing, bB = kVarRing;         // batched
+};
+
 struct DevHLevel {
   int N = 0, ne = 0;
   long long nnzA = 0;
@@ -147,6 +161,8 @@ struct pmg_hierarchy_s {
   char* arena = nullptr;
   std::vector<DevPLevel> dl;
   std::vector<DevHLevel> dh;
+  std::vector<PTune> ptune;
+  std::vector<HTune> htune;
   const double* cinv = nullptr;
   int sms = 0;
 };
@@ -383,35 +399,6 @@ bool lp_launch(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double*
   return false;
 }
 
-void lsolve(Ctx& c, int l, const double* b, double* y) {
-  const DevPLevel& D = c.h->dl[l];
-  launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
-    if (lp_launch(c, D.Llp, false, b, y, nullptr)) return;
-    const unsigned ep = next_epoch(c);
-    unsigned* cnt = next_counter(c);
-    pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, ep, cnt, c.w->err);
-  });
-}
-void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
-  const DevPLevel& D = c.h->dl[l];
-  launch(c, PMG_K_USOLVE, csr_bytes(D.nnzU, D.N) + (u ? 40.0 : 24.0) * D.N, [&] {
-    if (lp_launch(c, D.Ulp, true, y, e, u)) return;
-    const unsigned ep = next_epoch(c);
-    unsigned* cnt = next_counter(c);
-    pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, ep, cnt, c.w->err);
-  });
-}
-
-// u += U^{-1} L^{-1} r   (one ILUT smoothing step given r = f - A u)
-void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
-  lsolve(c, l, r, c.w->y[l]);
-  usolve(c, l, c.w->y[l], c.w->e[l], u);
-}
-
-// One lexicographic Gauss-Seidel sweep as a triangular solve:
-// forward  (D + L) x_new = b - U x_old,  backward  (D + U) x_new = b - L x_old.
-// The new values go to a scratch vector first (the solve polls its output for
-// readiness, so it cannot overwrite x in place) and are copied back.
 // Ring-kernel batched solve; false when the line does not fit in shared memory.
 template <class T>
 bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0) {
@@ -452,6 +439,47 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, c
   return true;
 }
 
+template <class T>
+void b_axpy(Ctx& c, int cls, long long n, const T* x, T* y) {
+  launch(c, cls, 3.0 * n * sizeof(T), [&] {
+    pmgk::k_axpy<T><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
+  });
+}
+
+void lsolve(Ctx& c, int l, const double* b, double* y) {
+  const DevPLevel& D = c.h->dl[l];
+  if (c.h->ptune[l].sL == kVarRing && b_lpc<double>(c, PMG_K_LSOLVE, D.Lc64, D.nnzL, false, b, y, 1)) return;
+  launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
+    if (lp_launch(c, D.Llp, false, b, y, nullptr)) return;
+    const unsigned ep = next_epoch(c);
+    unsigned* cnt = next_counter(c);
+    pmgk::k_lsolve<<<sync_grid(c), 256, 0, c.s>>>(D.L, b, y, c.w->flags, ep, cnt, c.w->err);
+  });
+}
+void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
+  const DevPLevel& D = c.h->dl[l];
+  if (c.h->ptune[l].sU == kVarRing && b_lpc<double>(c, PMG_K_USOLVE, D.Uc64, D.nnzU, true, y, e, 1)) {
+    if (u) b_axpy<double>(c, PMG_K_USOLVE, D.N, e, u);
+    return;
+  }
+  launch(c, PMG_K_USOLVE, csr_bytes(D.nnzU, D.N) + (u ? 40.0 : 24.0) * D.N, [&] {
+    if (lp_launch(c, D.Ulp, true, y, e, u)) return;
+    const unsigned ep = next_epoch(c);
+    unsigned* cnt = next_counter(c);
+    pmgk::k_usolve_update<<<sync_grid(c), 256, 0, c.s>>>(D.U, D.udinv, y, e, u, c.w->flags, ep, cnt, c.w->err);
+  });
+}
+
+// u += U^{-1} L^{-1} r   (one ILUT smoothing step given r = f - A u)
+void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
+  lsolve(c, l, r, c.w->y[l]);
+  usolve(c, l, c.w->y[l], c.w->e[l], u);
+}
+
+// One lexicographic Gauss-Seidel sweep as a triangular solve:
+// forward  (D + L) x_new = b - U x_old,  backward  (D + U) x_new = b - L x_old.
+// The new values go to a scratch vector first (the solve polls its output for
+// readiness, so it cannot overwrite x in place) and are copied back.
 void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   const DevHLevel& D = c.h->dh[j];
   double* t = c.w->hr[j];
@@ -460,7 +488,8 @@ void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   // the ring kernel in its one-vector form: the old-value part as an SpMV, the
   // new values by the line-pipelined solve with a 2-wide ring
   const pmgk::LpC<double>& ring = backward ? D.UpMc : D.Loc;
-  if (size_t(ring.nx + 64) * 32 * sizeof(double) <= kLpSmemCap) {
+  const unsigned char var = backward ? c.h->htune[j].gB : c.h->htune[j].gF;
+  if (var == kVarRing && size_t(ring.nx + 64) * 32 * sizeof(double) <= kLpSmemCap) {
     launch(c, PMG_K_GS, csr_bytes(D.nnzA / 2, D.N) + 24.0 * D.N,
            [&] { spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms); });
     b_lpc<double>(c, PMG_K_GS, ring, D.nnzA / 2, backward, t, xn, 1);
@@ -683,13 +712,6 @@ void b_lp(Ctx& c, int cls, const pmgk::LpB<T>& M, long long nnz, bool mirror, co
   });
 }
 
-template <class T>
-void b_axpy(Ctx& c, int cls, long long n, const T* x, T* y) {
-  launch(c, cls, 3.0 * n * sizeof(T), [&] {
-    pmgk::k_axpy<T><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
-  });
-}
-
 template <class TI, class TO>
 void b_cast(Ctx& c, long long n, const TI* x, TO* y) {
   pmgk::k_cast<TI, TO><<<grid_for(n, 256, c.h->sms * 16), 256, 0, c.s>>>(n, x, y);
@@ -704,7 +726,8 @@ void b_gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   double* xn = c.w->bhg[j];
   if (backward) b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Lo), D.nnzA / 2, x, b, t);
   else b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Up), D.nnzA / 2, x, b, t);
-  if (!b_lpc<double>(c, PMG_K_GS, backward ? D.UpMc : D.Loc, D.nnzA / 2, backward, t, xn))
+  const unsigned char var = backward ? c.h->htune[j].bB : c.h->htune[j].bF;
+  if (var != kVarRing || !b_lpc<double>(c, PMG_K_GS, backward ? D.UpMc : D.Loc, D.nnzA / 2, backward, t, xn))
     b_lp<double>(c, PMG_K_GS, backward ? D.UpMb : D.Lob, D.nnzA / 2, backward, t, xn, nullptr);
   cudaMemcpyAsync(x, xn, size_t(D.N) * R * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
 }
@@ -733,6 +756,21 @@ void b_hmg(Ctx& c, int j, const double* b, double* x) {
   b_gs(c, j, true, b, x);
 }
 
+// Batched triangular solve of level l (forward L, or mirrored U) with kernel variant `var`.
+template <class T>
+void b_tri(Ctx& c, int l, bool upper, unsigned char var, const T* b, T* x) {
+  const DevPLevel& D = c.h->dl[l];
+  const int cls = upper ? PMG_K_USOLVE : PMG_K_LSOLVE;
+  const long long nnz = upper ? D.nnzU : D.nnzL;
+  if constexpr (sizeof(T) == 4) {
+    if (var == kVarRing && b_lpc<float>(c, cls, upper ? D.Uc32 : D.Lc32, nnz, upper, b, x)) return;
+    b_lp<float>(c, cls, upper ? D.Ub32 : D.Lb32, nnz, upper, b, x, nullptr);
+  } else {
+    if (var == kVarRing && b_lpc<double>(c, cls, upper ? D.Uc64 : D.Lc64, nnz, upper, b, x)) return;
+    b_lp<double>(c, cls, upper ? D.Ub64 : D.Lb64, nnz, upper, b, x, nullptr);
+  }
+}
+
 // e = one V-cycle at p-level l applied to the right-hand side f with zero initial guess (precision T).
 template <class T>
 void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
@@ -741,18 +779,6 @@ void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
   const int nlev = int(c.h->dl.size()), R = c.w->R;
   const pmgk::TCsr<T> A = [&] {
     if constexpr (sizeof(T) == 4) return D.A32; else return as_t(D.A);
-  }();
-  const pmgk::LpB<T>& Lb = [&]() -> const pmgk::LpB<T>& {
-    if constexpr (sizeof(T) == 4) return D.Lb32; else return D.Lb64;
-  }();
-  const pmgk::LpB<T>& Ub = [&]() -> const pmgk::LpB<T>& {
-    if constexpr (sizeof(T) == 4) return D.Ub32; else return D.Ub64;
-  }();
-  const pmgk::LpC<T>& Lc = [&]() -> const pmgk::LpC<T>& {
-    if constexpr (sizeof(T) == 4) return D.Lc32; else return D.Lc64;
-  }();
-  const pmgk::LpC<T>& Uc = [&]() -> const pmgk::LpC<T>& {
-    if constexpr (sizeof(T) == 4) return D.Uc32; else return D.Uc64;
   }();
   const pmgk::TCsr<T> Res = [&] {
     if constexpr (sizeof(T) == 4) return D.Res32; else return as_t(D.Res);
@@ -768,9 +794,11 @@ void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
   auto smooth = [&](bool first) {
     const T* rr = f;
     if (!first) { b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r); rr = r; }
-    if (!b_lpc<T>(c, PMG_K_LSOLVE, Lc, D.nnzL, false, rr, y)) b_lp<T>(c, PMG_K_LSOLVE, Lb, D.nnzL, false, rr, y, nullptr);
-    if (b_lpc<T>(c, PMG_K_USOLVE, Uc, D.nnzU, true, y, t)) b_axpy<T>(c, PMG_K_USOLVE, (long long)D.N * R, t, e);
-    else b_lp<T>(c, PMG_K_USOLVE, Ub, D.nnzU, true, y, t, e);
+    const auto& tn = c.h->ptune[l];
+    const int pi = sizeof(T) == 4 ? 1 : 0;
+    b_tri<T>(c, l, false, tn.bL[pi], rr, y);
+    b_tri<T>(c, l, true, tn.bU[pi], y, t);
+    b_axpy<T>(c, PMG_K_USOLVE, (long long)D.N * R, t, e);
   };
   for (int m = 0; m < H.opt.nu_pre; ++m) smooth(m == 0);
   b_spmm<T, T, T, 0>(c, PMG_K_RESIDUAL, A, D.nnzA, e, f, r);
@@ -1040,6 +1068,14 @@ pmg_status pmg_info(pmg_handle h, pmg_info_t* info) {
   info->setup_ms_hmg = H.t_hmg;
   info->cycle_bytes = bytes;
   info->cycle_flops = flops;
+  for (size_t l = 0; l < H.lev.size(); ++l) {
+    const PTune t = l < h->ptune.size() ? h->ptune[l] : PTune{};
+    info->tune_p[l] = t.sL | (t.sU << 2) | (t.bL[0] << 4) | (t.bU[0] << 6) | (t.bL[1] << 8) | (t.bU[1] << 10);
+  }
+  for (size_t j = 0; j < H.hl.size(); ++j) {
+    const HTune t = j < h->htune.size() ? h->htune[j] : HTune{};
+    info->tune_h[j] = t.gF | (t.gB << 2) | (t.bF << 4) | (t.bB << 6);
+  }
   return PMG_OK;
 }
 
@@ -1132,6 +1168,8 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     h->dh.push_back(D);
   }
   h->cinv = reinterpret_cast<const double*>(base + h->off_cinv);
+  h->ptune.assign(h->dl.size(), PTune{});
+  h->htune.assign(h->dh.size(), HTune{});
   h->uploaded = true;
   return PMG_OK;
 }
@@ -1233,6 +1271,124 @@ pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F,
     return fail(PMG_ERR_ARG, "invalid batched solve argument (workspace holds " + std::to_string(ws->R ? ws->max_rhs : 0) + " right-hand sides)");
   return solve_batched_impl(h, ws, nrhs, F, U0, tol, max_iter, precision, U, iters, hist,
                             static_cast<cudaStream_t>(stream));
+}
+
+pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Ctx c{h, ws, s};
+  const bool prof = ws->prof;
+  ws->prof = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    ws->prof = prof;
+    return fail(PMG_ERR_CUDA, "event creation failed");
+  }
+  pmg_status err = PMG_OK;
+  // best of three timed runs after one warm-up run, in ms
+  auto timeit = [&](auto&& fn) -> double {
+    double best = 1e300;
+    for (int rep = 0; rep < 4 && err == PMG_OK; ++rep) {
+      if ((err = begin_launches(c)) != PMG_OK) break;
+      cudaEventRecord(e0, s);
+      fn();
+      cudaEventRecord(e1, s);
+      if ((err = finish_launches(c)) != PMG_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, double(ms));
+    }
+    return best;
+  };
+  auto fill = [&](auto* p, long long n) {
+    using T = std::remove_pointer_t<decltype(p)>;
+    pmgk::k_fill<T><<<grid_for(n, 256, h->sms * 16), 256, 0, s>>>(n, T(1), p);
+  };
+  auto pick = [&](unsigned char& slot, std::initializer_list<unsigned char> cands, auto&& fn) {
+    double best = 1e300;
+    unsigned char arg = slot;
+    for (unsigned char v : cands) {
+      slot = v;
+      const double t = timeit(fn);
+      if (t < best) { best = t; arg = v; }
+    }
+    slot = arg;
+  };
+  const size_t cap = kLpSmemCap;
+  for (size_t l = 0; l < h->dl.size() && err == PMG_OK; ++l) {
+    const DevPLevel& D = h->dl[l];
+    const int L = int(l);
+    fill(ws->f[l], D.N);
+    const bool ring_ok = size_t(D.Lc64.nx + 64) * 32 * sizeof(double) <= cap;
+    if (ring_ok) {
+      pick(h->ptune[l].sL, {kVarLp2, kVarRing}, [&] { lsolve(c, L, ws->f[l], ws->y[l]); });
+      pick(h->ptune[l].sU, {kVarLp2, kVarRing}, [&] { usolve(c, L, ws->f[l], ws->e[l], nullptr); });
+    }
+    if (ws->R) {
+      const long long nR = (long long)D.N * ws->R;
+      double* b64 = ws->bf[l];
+      float* b32 = reinterpret_cast<float*>(ws->br[l]);
+      fill(b64, nR);
+      fill(b32, nR);
+      for (int up = 0; up < 2; ++up) {
+        unsigned char& s64 = up ? h->ptune[l].bU[0] : h->ptune[l].bL[0];
+        unsigned char& s32 = up ? h->ptune[l].bU[1] : h->ptune[l].bL[1];
+        pick(s64, {kVarRing, kVarLines}, [&] { b_tri<double>(c, L, up, s64, b64, ws->by[l]); });
+        pick(s32, {kVarRing, kVarLines},
+             [&] { b_tri<float>(c, L, up, s32, b32, reinterpret_cast<float*>(ws->bt[l])); });
+      }
+    }
+  }
+  for (size_t j = 0; j + 1 < h->dh.size() && err == PMG_OK; ++j) {
+    const DevHLevel& D = h->dh[j];
+    const int J = int(j);
+    fill(ws->hb[j], D.N);
+    fill(ws->hx[j], D.N);
+    pick(h->htune[j].gF, {kVarLp2, kVarRing}, [&] { gs(c, J, false, ws->hb[j], ws->hx[j]); });
+    pick(h->htune[j].gB, {kVarLp2, kVarRing}, [&] { gs(c, J, true, ws->hb[j], ws->hx[j]); });
+    if (ws->R) {
+      const long long nR = (long long)D.N * ws->R;
+      fill(ws->bhb[j], nR);
+      fill(ws->bhx[j], nR);
+      pick(h->htune[j].bF, {kVarRing, kVarLines}, [&] { b_gs(c, J, false, ws->bhb[j], ws->bhx[j]); });
+      pick(h->htune[j].bB, {kVarRing, kVarLines}, [&] { b_gs(c, J, true, ws->bhb[j], ws->bhx[j]); });
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ws->prof = prof;
+  return err;
+}
+
+pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
+  if (!h || !tune_p || !tune_h) return fail(PMG_ERR_ARG, "null argument");
+  if (!h->uploaded) return fail(PMG_ERR_STATE, "hierarchy not uploaded");
+  auto field = [](int v, int k) { return (unsigned char)((v >> (2 * k)) & 3); };
+  for (size_t l = 0; l < h->dl.size(); ++l) {
+    const int v = tune_p[l];
+    if (field(v, 0) > kVarRing || field(v, 1) > kVarRing) return fail(PMG_ERR_ARG, "single-vector solves take variant 0 or 1");
+    for (int k = 2; k < 6; ++k)
+      if (field(v, k) == kVarLp2) return fail(PMG_ERR_ARG, "batched solves take variant 1 or 2");
+  }
+  for (size_t j = 0; j < h->dh.size(); ++j) {
+    const int v = tune_h[j];
+    if (field(v, 0) > kVarRing || field(v, 1) > kVarRing || field(v, 2) == kVarLp2 || field(v, 3) == kVarLp2 ||
+        field(v, 2) > kVarLines || field(v, 3) > kVarLines)
+      return fail(PMG_ERR_ARG, "invalid sweep variant");
+  }
+  for (size_t l = 0; l < h->dl.size(); ++l) {
+    const int v = tune_p[l];
+    PTune& t = h->ptune[l];
+    t.sL = field(v, 0); t.sU = field(v, 1);
+    t.bL[0] = field(v, 2); t.bU[0] = field(v, 3); t.bL[1] = field(v, 4); t.bU[1] = field(v, 5);
+  }
+  for (size_t j = 0; j < h->dh.size(); ++j) {
+    const int v = tune_h[j];
+    HTune& t = h->htune[j];
+    t.gF = field(v, 0); t.gB = field(v, 1); t.bF = field(v, 2); t.bB = field(v, 3);
+  }
+  return PMG_OK;
 }
 
 pmg_status pmg_apply(pmg_handle h, pmg_ws ws, int op, int level, const double* x, const double* b, double* y,

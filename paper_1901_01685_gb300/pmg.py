@@ -31,7 +31,8 @@ PMG_PREC_FP64, PMG_PREC_MIXED = 0, 1
 
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
-           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_apply",
+           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_autotune", "pmg_set_kernels",
+           "pmg_apply",
            "pmg_export_csr",
            "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_lsolve_noalloc",
            "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
@@ -56,7 +57,7 @@ class pmg_info_t(C.Structure):
                 ("n_h", _L16), ("nnz_h", _LL16), ("depth_gs", _L16), ("device_bytes", C.c_size_t),
                 ("setup_ms_assembly", C.c_double), ("setup_ms_ilut", C.c_double),
                 ("setup_ms_transfer", C.c_double), ("setup_ms_hmg", C.c_double),
-                ("cycle_bytes", C.c_double), ("cycle_flops", C.c_double)]
+                ("cycle_bytes", C.c_double), ("cycle_flops", C.c_double), ("tune_p", _L16), ("tune_h", _L16)]
 
     def as_dict(self) -> dict:
         nl, nh = self.nlevels, self.nhlevels
@@ -67,6 +68,12 @@ class pmg_info_t(C.Structure):
             d[k] = list(getattr(self, k))[:nl]
         for k in ("n_h", "nnz_h", "depth_gs"):
             d[k] = list(getattr(self, k))[:nh]
+        names = ("windowed", "ring", "lines")
+        d["kernels_p"] = [{f: names[(v >> (2 * b)) & 3] for b, f in enumerate(
+            ("single_L", "single_U", "batched64_L", "batched64_U", "batched32_L", "batched32_U"))}
+            for v in list(self.tune_p)[:nl]]
+        d["kernels_h"] = [{f: names[(v >> (2 * b)) & 3] for b, f in enumerate(
+            ("single_fwd", "single_bwd", "batched_fwd", "batched_bwd"))} for v in list(self.tune_h)[:nh]]
         return d
 
 
@@ -103,6 +110,8 @@ def lib():
         L.pmg_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
         L.pmg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, dp, ip, dp, C.c_int, vp]
         L.pmg_solve_batched.argtypes = [vp, vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int, vp, ip, dp, vp]
+        L.pmg_autotune.argtypes = [vp, vp, vp]
+        L.pmg_set_kernels.argtypes = [vp, ip, ip]
         L.pmg_apply.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
         L.pmg_export_csr.argtypes = [vp, C.c_int, C.c_int, ip, ip, C.POINTER(C.c_longlong), ip, ip, dp]
         L.pmg_export_lumped.argtypes = [vp, C.c_int, dp]
@@ -232,6 +241,16 @@ def pmg_solve_batched(h, ws, nrhs, F, U0, rel_tol, max_iter, precision, U, strea
     return iters, hist[: int(iters.max(initial=0))].copy(), st
 
 
+def pmg_autotune(h, ws, stream=None):
+    _check(lib().pmg_autotune(h, ws, _stream(stream)), "pmg_autotune")
+
+
+def pmg_set_kernels(h, tune_p, tune_h):
+    tp = np.ascontiguousarray(tune_p, dtype=np.int32)
+    th = np.ascontiguousarray(tune_h, dtype=np.int32)
+    _check(lib().pmg_set_kernels(h, _ip(tp), _ip(th)), "pmg_set_kernels")
+
+
 def pmg_apply(h, ws, op, level, x, b, y, stream=None):
     _check(lib().pmg_apply(h, ws, op, level, _ptr(x), _ptr(b), _ptr(y), _stream(stream)), "pmg_apply")
 
@@ -328,6 +347,20 @@ class Solver:
             u = torch.empty_like(u0)
         it, hist, st = pmg_solve(self.h, self.ws, f, u0, rel_tol, max_iter, u, allow=allow)
         return u, it, hist, st
+
+    def autotune(self):
+        """Times the kernel variants of every solve on this device and keeps the fastest."""
+        pmg_autotune(self.h, self.ws)
+        self.info = pmg_info(self.h).as_dict()
+        return self.info["kernels_p"], self.info["kernels_h"]
+
+    def set_kernels(self, single=1, batched=1, sweep_single=1, sweep_batched=1):
+        """One variant for every level: single-vector solves 0 (windowed) or 1
+        (ring); batched solves 1 (ring) or 2 (lines per CTA)."""
+        tp = single | (single << 2) | (batched << 4) | (batched << 6) | (batched << 8) | (batched << 10)
+        th = sweep_single | (sweep_single << 2) | (sweep_batched << 4) | (sweep_batched << 6)
+        pmg_set_kernels(self.h, [tp] * self.info["nlevels"], [th] * self.info["nhlevels"])
+        self.info = pmg_info(self.h).as_dict()
 
     def solve_batched(self, F, U0, rel_tol=1e-8, max_iter=100, precision=PMG_PREC_FP64, U=None, allow=()):
         """F, U0: (nrhs, n) float64 device tensors.  Returns (U, iters, hist, status)."""
