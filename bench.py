@@ -31,6 +31,10 @@ METRIC = "MDOF*iter/s to 1e-8 relres (plain FP64)"
 UNIT = "MDOF*iter/s"
 DEGREES = (2, 3, 4, 5)
 LOG2H = 8
+SERVING_KEYS = [(d, p, k) for d in (0, 1) for k in (5, 6, 7) for p in (2, 3, 4, 5)] + [(2, 2, 4), (2, 3, 4)]
+SERVING_REQUESTS = 256
+SERVING_RATE = 400.0          # requests per second
+SERVING_SLOTS = 32
 BATCHED_CASE = (0, 4, 9)     # quarter annulus, p = 4, h = 2^-9
 BATCHED_NRHS = 64
 WORKLOAD = "quarter annulus Poisson, h=2^-8, p=2..5, indirect p-MG V-cycle, ILUT(1e-12,1), 1e-8 relres"
@@ -255,6 +259,36 @@ def _batched_section(args, dist, flush, stream, world):
                             "max_final_fp64_relres": max(relres)}}
 
 
+def _serving_section(args):
+    """Continuous-batching server: a seeded Poisson stream of requests over
+    2D and 3D problem keys (1-16 right-hand sides each), served once with plain
+    FP64 cycles and once with FP32-inner cycles, same arrivals; p50/p99
+    latency (arrival to result on the host) and solves/s.  Hierarchies are set
+    up and made resident before the stream starts (setup is timed separately,
+    as in the paper's App. C)."""
+    from paper_1901_01685_gb300 import pmg, serve
+    keys = SERVING_KEYS
+    out = {"workload": f"{SERVING_REQUESTS} requests, Poisson arrivals at {SERVING_RATE:.0f}/s, keys uniform over "
+                       f"{len(keys)} (domain, p, h): quarter annulus and unit square h=2^-5..2^-7, p=2..5; "
+                       "unit cube h=2^-4, p=2..3; 1-16 right-hand sides each, 1e-8 relres",
+           "slots_per_key": SERVING_SLOTS}
+    arrivals = serve.poisson_arrivals(SERVING_REQUESTS, SERVING_RATE, seed=7)
+    for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED)):
+        be = serve.GpuBackend(autotune=not args.no_autotune)
+        srv = serve.Server(be, slots=SERVING_SLOTS, precision=prec)
+        t0 = time.perf_counter()
+        srv.prewarm(keys)
+        t_setup = time.perf_counter() - t0
+        rhs = {k: (srv.keys[k].handle["S"].rhs(), srv.keys[k].handle["S"].N) for k in keys}
+        reqs = serve.request_mix(keys, SERVING_REQUESTS, lambda k: rhs[k], seed=11, max_rhs=16)
+        stats = serve.run_stream(srv, reqs, arrivals)
+        stats["setup_s"] = t_setup
+        out[name] = stats
+        srv.close()
+    out["mixed_vs_fp64_solves_per_s"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -372,6 +406,7 @@ def run_ours(args):
     e2e_value = job_value(e2e_units, world, t_e2e)
 
     batched = None if args.no_batched or args.case else _batched_section(args, dist, flush, stream, world)
+    serving = None if args.no_serving or args.case or rank != 0 else _serving_section(args)
 
     if rank != 0:
         return
@@ -401,6 +436,8 @@ def run_ours(args):
     }
     if batched is not None:
         line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline and not args.case:
         v, secs, solves = _oracle_sample(args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -420,6 +457,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the many-right-hand-side section")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel variants")
+    ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving section")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -179,6 +179,41 @@ pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F_
                              double rel_tol, int max_iter, int precision, double* U_dev, int* iters_host,
                              double* hist_host, void* stream);
 
+/* Continuous batching (the paper has no counterpart).  The max_rhs slots of a
+ * workspace (created with max_rhs >= 2) are filled, iterated and drained
+ * independently, so right-hand sides can join and leave a running batch
+ * between V-cycles.  Every slot follows exactly the iteration of
+ * pmg_solve_batched; its result depends neither on the other slots nor on
+ * when it was loaded.  All slot calls of one workspace go to one stream and
+ * do not block, except pmg_slots_wait.
+ *
+ * pmg_slots_load: copies n right-hand sides and initial guesses (device,
+ *   right-hand side k contiguous at offset k*n[0]) into slots slot0..slot0+n-1
+ *   (none of them active), computes their initial residual norms and makes
+ *   them active (a slot with a zero initial residual is reported converged
+ *   with 0 cycles after the next cycle's wait).
+ * pmg_slots_cycle: one V-cycle (PMG_PREC_FP64 or PMG_PREC_MIXED, as in
+ *   pmg_solve_batched) for every active slot, then each one's stopping test
+ *   (relative residual < rel_tol: converged; > 1e10: diverged).  A no-op when
+ *   no slot is active.
+ * pmg_slots_wait: when the last cycle has finished (at once if
+ *   blocking), sets *ready = 1 and copies per slot (arrays of max_rhs entries,
+ *   each may be NULL) the last relative residual, the state (0 free, 1 active,
+ *   2 converged, 3 diverged) and the cycles done; otherwise *ready = 0.
+ * pmg_slots_read: copies the current solutions of n slots out (device,
+ *   stream-ordered).
+ * pmg_slots_release: frees n slots (an active slot is cancelled).
+ * Errors: PMG_ERR_ARG, PMG_ERR_BUSY (load / cycle / release while a cycle
+ * has not been waited for, or load into an active slot),
+ * PMG_ERR_TIMEOUT (reported by pmg_slots_wait), PMG_ERR_CUDA. */
+pmg_status pmg_slots_load(pmg_handle h, pmg_ws ws, int slot0, int n, const double* F_dev, const double* U0_dev,
+                          void* stream);
+pmg_status pmg_slots_cycle(pmg_handle h, pmg_ws ws, int precision, double rel_tol, void* stream);
+pmg_status pmg_slots_wait(pmg_handle h, pmg_ws ws, int blocking, int* ready, double* relres_host, int* state_host,
+                          int* iters_host);
+pmg_status pmg_slots_read(pmg_handle h, pmg_ws ws, int slot0, int n, double* U_dev, void* stream);
+pmg_status pmg_slots_release(pmg_handle h, pmg_ws ws, int slot0, int n, void* stream);
+
 /* Kernel autotuner (the paper has no counterpart): times every available
  * kernel variant of each triangular solve and Gauss-Seidel sweep of the
  * hierarchy on the current device, single-vector and (if the workspace holds

@@ -497,6 +497,61 @@ __global__ void k_norm_finalize_b(int nparts, int R, const double* __restrict__ 
   }
 }
 
+// Continuous-batching slot bookkeeping.  state: 0 free, 1 active, 2 converged,
+// 3 diverged; an active slot has mask 1 (its u is updated by the cycle).
+__global__ void k_slots_copy_in(int n, int nload, int R, int slot0, const double* __restrict__ src,
+                                double* __restrict__ dst) {
+  const long long total = (long long)n * nload;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long i = t / nload;
+    const int c = (int)(t % nload);
+    dst[i * R + slot0 + c] = src[(size_t)c * n + i];
+  }
+}
+__global__ void k_slots_copy_out(int n, int nread, int R, int slot0, const double* __restrict__ src,
+                                 double* __restrict__ dst) {
+  const long long total = (long long)n * nread;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / n);
+    const long long i = t % n;
+    dst[t] = src[i * R + slot0 + c];
+  }
+}
+// r0 of newly loaded slots; a zero initial residual converges at once.
+__global__ void k_slots_start(int nparts, int R, int slot0, int nload, const double* __restrict__ partial, double* r0,
+                              double* relres, double* mask, int* state, int* iters) {
+  for (int c = slot0 + blockIdx.x * blockDim.x + threadIdx.x; c < slot0 + nload; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * R + c];
+    const double nrm = sqrt(s);
+    r0[c] = nrm;
+    iters[c] = 0;
+    relres[c] = nrm > 0.0 ? 1.0 : 0.0;
+    state[c] = nrm > 0.0 ? 1 : 2;
+    mask[c] = nrm > 0.0 ? 1.0 : 0.0;
+  }
+}
+// After a cycle: relative residual of every active slot, then its stopping test (Sec. 5).
+__global__ void k_slots_update(int nparts, int R, double tol, const double* __restrict__ partial,
+                               const double* __restrict__ r0, double* relres, double* mask, int* state, int* iters) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) {
+    if (state[c] != 1) continue;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * R + c];
+    const double rel = sqrt(s) / r0[c];
+    relres[c] = rel;
+    iters[c] += 1;
+    if (rel < tol) { state[c] = 2; mask[c] = 0.0; }
+    else if (!(rel <= 1e10)) { state[c] = 3; mask[c] = 0.0; }
+  }
+}
+__global__ void k_slots_release(int R, int slot0, int n, double* mask, int* state) {
+  for (int c = slot0 + blockIdx.x * blockDim.x + threadIdx.x; c < slot0 + n; c += gridDim.x * blockDim.x) {
+    state[c] = 0;
+    mask[c] = 0.0;
+  }
+}
+
 // Layout conversions between the caller's [nrhs][n] and the internal [n][R].
 __global__ void k_to_rows(int n, int nrhs, int R, const double* __restrict__ src, double* __restrict__ dst) {
   const long long total = (long long)n * R;

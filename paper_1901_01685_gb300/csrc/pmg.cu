@@ -180,6 +180,15 @@ struct pmg_workspace_s {
   std::vector<double*> bhb, bhx, bhr, bhg, bht; // per P1 level (FP64)
   double *bF = nullptr, *bU = nullptr, *bR = nullptr;
   double *br0 = nullptr, *brel = nullptr, *bmask = nullptr, *bpart = nullptr;
+  // continuous batching: per-slot state and iteration count (device), and the
+  // pinned host mirror the end of each cycle is copied into
+  int *bstate = nullptr, *biters = nullptr;
+  struct SlotMirror { double* relres; int* state; int* iters; unsigned* err; };
+  SlotMirror hm{nullptr, nullptr, nullptr, nullptr};
+  void* hm_block = nullptr;
+  std::vector<int> slot_state;      // host view of the slot states after the last wait / load
+  cudaEvent_t slot_ev = nullptr;
+  bool slot_pending = false;
   unsigned* flags = nullptr;
   unsigned long long* lprog = nullptr;   // per-line progress words of the line-pipelined solves
   unsigned* counters = nullptr;
@@ -203,6 +212,8 @@ struct pmg_workspace_s {
   long long launches = 0;
   ~pmg_workspace_s() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (slot_ev) cudaEventDestroy(slot_ev);
+    if (hm_block) cudaFreeHost(hm_block);
   }
 };
 
@@ -214,7 +225,7 @@ struct WsLayout {
   size_t flags, lprog, counters, err, partial, r0, hist, f_in, u_io;
   int R = 0;
   std::vector<size_t> bf, be, br, by, bt, bhb, bhx, bhr, bhg, bht;
-  size_t bF = 0, bU = 0, bR = 0, br0 = 0, brel = 0, bmask = 0, bpart = 0;
+  size_t bF = 0, bU = 0, bR = 0, br0 = 0, brel = 0, bmask = 0, bpart = 0, bstate = 0, biters = 0;
 };
 
 WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
@@ -250,6 +261,8 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
     W.bF = take(b0); W.bU = take(b0); W.bR = take(b0);
     W.br0 = take(W.R * sizeof(double)); W.brel = take(W.R * sizeof(double)); W.bmask = take(W.R * sizeof(double));
     W.bpart = take(size_t(pmgk::kNormBlocks) * W.R * sizeof(double));
+    W.bstate = take(W.R * sizeof(int));
+    W.biters = take(W.R * sizeof(int));
   }
   W.flags = take(size_t(maxN) * sizeof(unsigned));
   int maxLines = 1;
@@ -903,6 +916,30 @@ pmg_status solve_batched_impl(pmg_handle h, pmg_ws ws, int nrhs, const double* F
   return result;
 }
 
+// Continuous batching: end of every slot operation.  The per-slot relative
+// residual, state and iteration count and the error words are copied into
+// the workspace's pinned mirror and an event marks the point; pmg_slots_wait
+// reads the mirror once the event has passed.
+pmg_status slots_snapshot(Ctx& c) {
+  pmg_ws w = c.w;
+  const int R = w->R;
+  PMG_CUDA(cudaMemcpyAsync(w->hm.relres, w->brel, R * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(w->hm.state, w->bstate, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(w->hm.iters, w->biters, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(w->hm.err, w->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaEventRecord(w->slot_ev, c.s));
+  PMG_CUDA(cudaGetLastError());
+  w->slot_pending = true;
+  return PMG_OK;
+}
+
+pmg_status slots_check(pmg_handle h, pmg_ws ws) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  if (ws->R == 0) return fail(PMG_ERR_ARG, "workspace has no right-hand-side slots (max_rhs < 2)");
+  return PMG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1218,6 +1255,22 @@ pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t byt
   if (W.R) {
     w->bF = P(W.bF); w->bU = P(W.bU); w->bR = P(W.bR);
     w->br0 = P(W.br0); w->brel = P(W.brel); w->bmask = P(W.bmask); w->bpart = P(W.bpart);
+    w->bstate = reinterpret_cast<int*>(base + W.bstate);
+    w->biters = reinterpret_cast<int*>(base + W.biters);
+    // pinned host mirror of the slot state (host memory; the library allocates no device memory)
+    const size_t hb = size_t(W.R) * (sizeof(double) + 2 * sizeof(int)) + 4 * sizeof(unsigned);
+    if (cudaHostAlloc(&w->hm_block, hb, cudaHostAllocDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w->slot_ev, cudaEventDisableTiming) != cudaSuccess) {
+      delete w;
+      return fail(PMG_ERR_CUDA, "pinned slot mirror / event creation failed");
+    }
+    char* hbp = static_cast<char*>(w->hm_block);
+    w->hm.relres = reinterpret_cast<double*>(hbp);
+    w->hm.state = reinterpret_cast<int*>(hbp + size_t(W.R) * sizeof(double));
+    w->hm.iters = w->hm.state + W.R;
+    w->hm.err = reinterpret_cast<unsigned*>(w->hm.iters + W.R);
+    std::memset(w->hm_block, 0, hb);
+    w->slot_state.assign(size_t(W.R), 0);
   }
   w->flags = reinterpret_cast<unsigned*>(base + W.flags);
   w->lprog = reinterpret_cast<unsigned long long*>(base + W.lprog);
@@ -1271,6 +1324,118 @@ pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F,
     return fail(PMG_ERR_ARG, "invalid batched solve argument (workspace holds " + std::to_string(ws->R ? ws->max_rhs : 0) + " right-hand sides)");
   return solve_batched_impl(h, ws, nrhs, F, U0, tol, max_iter, precision, U, iters, hist,
                             static_cast<cudaStream_t>(stream));
+}
+
+pmg_status pmg_slots_load(pmg_handle h, pmg_ws ws, int slot0, int n, const double* F, const double* U0,
+                          void* stream) {
+  pmg_status st = slots_check(h, ws);
+  if (st != PMG_OK) return st;
+  if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs || !F || !U0) return fail(PMG_ERR_ARG, "invalid slot range");
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
+  for (int k = slot0; k < slot0 + n; ++k)
+    if (ws->slot_state[k] == 1) return fail(PMG_ERR_BUSY, "slot " + std::to_string(k) + " is active");
+  Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
+  const int N = h->dl[0].N, R = ws->R;
+  const DevPLevel& D = h->dl[0];
+  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, F, ws->bF);
+  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, U0, ws->bU);
+  ws->launches += 2;
+  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
+    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
+    pmgk::k_slots_start<<<1, 128, 0, c.s>>>(pmgk::kNormBlocks, R, slot0, n, ws->bpart, ws->br0, ws->brel,
+                                            ws->bmask, ws->bstate, ws->biters);
+  });
+  for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 1;
+  PMG_CUDA(cudaGetLastError());
+  return PMG_OK;
+}
+
+pmg_status pmg_slots_cycle(pmg_handle h, pmg_ws ws, int precision, double rel_tol, void* stream) {
+  pmg_status st = slots_check(h, ws);
+  if (st != PMG_OK) return st;
+  if (!(rel_tol > 0) || (precision != PMG_PREC_FP64 && precision != PMG_PREC_MIXED))
+    return fail(PMG_ERR_ARG, "invalid cycle argument");
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
+  if (std::find(ws->slot_state.begin(), ws->slot_state.end(), 1) == ws->slot_state.end()) return PMG_OK;
+  Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
+  const int N = h->dl[0].N, R = ws->R;
+  const DevPLevel& D = h->dl[0];
+  if ((st = begin_launches(c)) != PMG_OK) return st;
+  if (precision == PMG_PREC_MIXED) {
+    float* r32 = reinterpret_cast<float*>(ws->bf[0]);
+    float* e32 = reinterpret_cast<float*>(ws->be[0]);
+    b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
+    b_vcycle0<float>(c, 0, r32, e32);
+    pmgk::k_masked_update<float><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, e32, ws->bmask,
+                                                                                                 ws->bU);
+  } else {
+    b_vcycle0<double>(c, 0, ws->bR, ws->be[0]);
+    pmgk::k_masked_update<double><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, ws->be[0],
+                                                                                                  ws->bmask, ws->bU);
+  }
+  ++ws->launches;
+  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
+    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
+    pmgk::k_slots_update<<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, rel_tol, ws->bpart, ws->br0,
+                                                           ws->brel, ws->bmask, ws->bstate, ws->biters);
+  });
+  return slots_snapshot(c);
+}
+
+pmg_status pmg_slots_wait(pmg_handle h, pmg_ws ws, int blocking, int* ready, double* relres, int* state, int* iters) {
+  pmg_status st = slots_check(h, ws);
+  if (st != PMG_OK) return st;
+  if (!ready) return fail(PMG_ERR_ARG, "ready is NULL");
+  *ready = 0;
+  if (ws->slot_pending) {
+    const cudaError_t q = blocking ? cudaEventSynchronize(ws->slot_ev) : cudaEventQuery(ws->slot_ev);
+    if (q == cudaErrorNotReady) return PMG_OK;
+    if (q != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(q));
+    ws->slot_pending = false;
+    collect_profile(ws);
+    for (int k = 0; k < ws->R; ++k) ws->slot_state[k] = ws->hm.state[k];
+    if (ws->hm.err[0]) {
+      cudaMemset(ws->err, 0, 4 * sizeof(unsigned));
+      char buf[160];
+      std::snprintf(buf, sizeof(buf),
+                    "a device-side dependency wait expired (wait sites 0x%x; first: site 0x%x, item %u, row %u, warp %u)",
+                    ws->hm.err[0], ws->hm.err[1], ws->hm.err[2], ws->hm.err[3] >> 8, ws->hm.err[3] & 0xffu);
+      return fail(PMG_ERR_TIMEOUT, buf);
+    }
+  }
+  *ready = 1;
+  for (int k = 0; k < ws->max_rhs; ++k) {
+    if (relres) relres[k] = ws->hm.relres[k];
+    if (state) state[k] = ws->slot_state[k];
+    if (iters) iters[k] = ws->hm.iters[k];
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_slots_read(pmg_handle h, pmg_ws ws, int slot0, int n, double* U, void* stream) {
+  pmg_status st = slots_check(h, ws);
+  if (st != PMG_OK) return st;
+  if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs || !U) return fail(PMG_ERR_ARG, "invalid slot range");
+  const int N = h->dl[0].N;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  pmgk::k_slots_copy_out<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, s>>>(N, n, ws->R, slot0, ws->bU, U);
+  ++ws->launches;
+  PMG_CUDA(cudaGetLastError());
+  return PMG_OK;
+}
+
+pmg_status pmg_slots_release(pmg_handle h, pmg_ws ws, int slot0, int n, void* stream) {
+  pmg_status st = slots_check(h, ws);
+  if (st != PMG_OK) return st;
+  if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs) return fail(PMG_ERR_ARG, "invalid slot range");
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
+  pmgk::k_slots_release<<<1, 128, 0, static_cast<cudaStream_t>(stream)>>>(ws->R, slot0, n, ws->bmask, ws->bstate);
+  ++ws->launches;
+  PMG_CUDA(cudaGetLastError());
+  for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 0;
+  return PMG_OK;
 }
 
 pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {

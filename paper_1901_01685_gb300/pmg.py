@@ -31,8 +31,8 @@ PMG_PREC_FP64, PMG_PREC_MIXED = 0, 1
 
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
-           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_autotune", "pmg_set_kernels",
-           "pmg_apply",
+           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_slots_load", "pmg_slots_cycle",
+           "pmg_slots_wait", "pmg_slots_read", "pmg_slots_release", "pmg_autotune", "pmg_set_kernels", "pmg_apply",
            "pmg_export_csr",
            "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_lsolve_noalloc",
            "pmg_ws_destroy", "pmg_destroy", "pmg_last_error")
@@ -110,6 +110,11 @@ def lib():
         L.pmg_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
         L.pmg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, dp, ip, dp, C.c_int, vp]
         L.pmg_solve_batched.argtypes = [vp, vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int, vp, ip, dp, vp]
+        L.pmg_slots_load.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
+        L.pmg_slots_cycle.argtypes = [vp, vp, C.c_int, C.c_double, vp]
+        L.pmg_slots_wait.argtypes = [vp, vp, C.c_int, ip, dp, ip, ip]
+        L.pmg_slots_read.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
+        L.pmg_slots_release.argtypes = [vp, vp, C.c_int, C.c_int, vp]
         L.pmg_autotune.argtypes = [vp, vp, vp]
         L.pmg_set_kernels.argtypes = [vp, ip, ip]
         L.pmg_apply.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp, vp]
@@ -241,6 +246,37 @@ def pmg_solve_batched(h, ws, nrhs, F, U0, rel_tol, max_iter, precision, U, strea
     return iters, hist[: int(iters.max(initial=0))].copy(), st
 
 
+PMG_SLOT_FREE, PMG_SLOT_ACTIVE, PMG_SLOT_CONVERGED, PMG_SLOT_DIVERGED = 0, 1, 2, 3
+
+
+def pmg_slots_load(h, ws, slot0, F, U0, stream=None):
+    """F, U0: device tensors (n, N) loaded into slots slot0 .. slot0+n-1."""
+    _check(lib().pmg_slots_load(h, ws, slot0, F.shape[0], _ptr(F), _ptr(U0), _stream(stream)), "pmg_slots_load")
+
+
+def pmg_slots_cycle(h, ws, precision, rel_tol=1e-8, stream=None):
+    _check(lib().pmg_slots_cycle(h, ws, precision, rel_tol, _stream(stream)), "pmg_slots_cycle")
+
+
+def pmg_slots_wait(h, ws, max_rhs, blocking=True):
+    """Returns None while the last slot operation runs, else (relres, state, iters) per slot."""
+    ready = C.c_int()
+    rel = np.zeros(max_rhs)
+    state = np.zeros(max_rhs, np.int32)
+    iters = np.zeros(max_rhs, np.int32)
+    _check(lib().pmg_slots_wait(h, ws, int(bool(blocking)), C.byref(ready), _dp(rel), _ip(state), _ip(iters)),
+           "pmg_slots_wait")
+    return (rel, state, iters) if ready.value else None
+
+
+def pmg_slots_read(h, ws, slot0, U, stream=None):
+    _check(lib().pmg_slots_read(h, ws, slot0, U.shape[0], _ptr(U), _stream(stream)), "pmg_slots_read")
+
+
+def pmg_slots_release(h, ws, slot0, n, stream=None):
+    _check(lib().pmg_slots_release(h, ws, slot0, n, _stream(stream)), "pmg_slots_release")
+
+
 def pmg_autotune(h, ws, stream=None):
     _check(lib().pmg_autotune(h, ws, _stream(stream)), "pmg_autotune")
 
@@ -317,11 +353,14 @@ class Solver:
     def __init__(self, domain: int, p: int, log2_inv_h: int, projection: int = PMG_PROJ_INDIRECT,
                  exact: int = PMG_U_SINPROD, drop_tol: float = 1e-12, fill_factor: float = 1.0,
                  nu_pre: int = 1, nu_post: int = 1, coarse_cycles: int = 2, device: str = "cuda",
-                 upload: bool = True, max_rhs: int = 1):
-        opt = pmg_default_options()
-        opt.projection, opt.exact, opt.drop_tol, opt.fill_factor = projection, exact, drop_tol, fill_factor
-        opt.nu_pre, opt.nu_post, opt.coarse_cycles = nu_pre, nu_post, coarse_cycles
-        self.h = pmg_setup(domain, p, log2_inv_h, opt)
+                 upload: bool = True, max_rhs: int = 1, handle=None):
+        if handle is not None:
+            self.h = handle            # adopt a hierarchy set up elsewhere (pmg_setup)
+        else:
+            opt = pmg_default_options()
+            opt.projection, opt.exact, opt.drop_tol, opt.fill_factor = projection, exact, drop_tol, fill_factor
+            opt.nu_pre, opt.nu_post, opt.coarse_cycles = nu_pre, nu_post, coarse_cycles
+            self.h = pmg_setup(domain, p, log2_inv_h, opt)
         self.info = pmg_info(self.h).as_dict()
         self.N = self.info["n"][0]
         self.arena = self.mem = self.ws = None
