@@ -286,6 +286,7 @@ typedef struct {
   long long launches[PMG_NKERN]; /* launches per class (profiling on) */
   double bytes[PMG_NKERN];       /* summed algorithmic DRAM bytes per class (profiling on) */
   long long total_launches;      /* all kernel launches issued through this workspace */
+  long long graph_launches;      /* V-cycles replayed as one CUDA graph (counted in total_launches by their kernels) */
 } pmg_stats_t;
 
 /* Turns per-launch CUDA-event timing on (enable != 0) or off for `ws`.  Events

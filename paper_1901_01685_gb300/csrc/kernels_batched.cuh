@@ -485,18 +485,6 @@ __global__ void k_sqnorm_partial_b(int n, int R, const double* __restrict__ r, d
     partial[(size_t)blockIdx.x * R + c] = s;
   }
 }
-// MODE 0: r0[c] = sqrt(sum); MODE 1: out[c] = sqrt(sum) / r0[c] (0 if r0 == 0).
-template <int MODE>
-__global__ void k_norm_finalize_b(int nparts, int R, const double* __restrict__ partial, double* r0, double* out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * R + c];
-    const double nrm = sqrt(s);
-    if (MODE == 0) r0[c] = nrm;
-    else out[c] = r0[c] > 0.0 ? nrm / r0[c] : 0.0;
-  }
-}
-
 // Continuous-batching slot bookkeeping.  state: 0 free, 1 active, 2 converged,
 // 3 diverged; an active slot has mask 1 (its u is updated by the cycle).
 __global__ void k_slots_copy_in(int n, int nload, int R, int slot0, const double* __restrict__ src,
@@ -549,24 +537,6 @@ __global__ void k_slots_release(int R, int slot0, int n, double* mask, int* stat
   for (int c = slot0 + blockIdx.x * blockDim.x + threadIdx.x; c < slot0 + n; c += gridDim.x * blockDim.x) {
     state[c] = 0;
     mask[c] = 0.0;
-  }
-}
-
-// Layout conversions between the caller's [nrhs][n] and the internal [n][R].
-__global__ void k_to_rows(int n, int nrhs, int R, const double* __restrict__ src, double* __restrict__ dst) {
-  const long long total = (long long)n * R;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const long long i = t / R;
-    const int c = (int)(t % R);
-    dst[t] = c < nrhs ? src[(size_t)c * n + i] : 0.0;
-  }
-}
-__global__ void k_from_rows(int n, int nrhs, int R, const double* __restrict__ src, double* __restrict__ dst) {
-  const long long total = (long long)n * nrhs;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(t / n);
-    const long long i = t % n;
-    dst[t] = src[i * R + c];
   }
 }
 

@@ -163,6 +163,7 @@ struct pmg_hierarchy_s {
   std::vector<DevHLevel> dh;
   std::vector<PTune> ptune;
   std::vector<HTune> htune;
+  unsigned tune_epoch = 0;           // bumped when a kernel choice changes (captured graphs go stale)
   const double* cinv = nullptr;
   int sms = 0;
 };
@@ -189,6 +190,11 @@ struct pmg_workspace_s {
   std::vector<int> slot_state;      // host view of the slot states after the last wait / load
   cudaEvent_t slot_ev = nullptr;
   bool slot_pending = false;
+  // CUDA-graph replay of the slot cycle, per precision
+  struct CycleGraph { cudaGraphExec_t exec = nullptr; double tol = 0; unsigned epoch = 0; long long launches = 0; int eager = 0; };
+  CycleGraph cyc[2];
+  bool graphs = true;
+  long long graph_launches = 0;
   unsigned* flags = nullptr;
   unsigned long long* lprog = nullptr;   // per-line progress words of the line-pipelined solves
   unsigned* counters = nullptr;
@@ -213,6 +219,8 @@ struct pmg_workspace_s {
   ~pmg_workspace_s() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (slot_ev) cudaEventDestroy(slot_ev);
+    for (auto& g : cyc)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     if (hm_block) cudaFreeHost(hm_block);
   }
 };
@@ -845,92 +853,193 @@ void b_vcycle0(Ctx& c, int l, const T* f, T* e) {
   for (int m = 0; m < H.opt.nu_post; ++m) smooth(false);
 }
 
-void b_norms(Ctx& c, int n, const double* r, int mode) {
-  const int R = c.w->R;
-  launch(c, PMG_K_NORM, 8.0 * n * R, [&] {
-    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(n, R, r, c.w->bpart);
-    if (mode == 0) pmgk::k_norm_finalize_b<0><<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, c.w->bpart, c.w->br0, nullptr);
-    else pmgk::k_norm_finalize_b<1><<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, c.w->bpart, c.w->br0, c.w->brel);
+
+// ---------------------------------------------------------------------------
+// Slots (continuous batching) and the batched solve built on them.  A slot is
+// one column of the [row][R] batch with a device-side state (free, active,
+// converged, diverged), iteration count and update mask; a cycle updates only
+// active slots, and its stopping test runs on the device.  The end of a cycle
+// copies the per-slot state into the workspace's pinned mirror.
+// ---------------------------------------------------------------------------
+pmg_status slots_load_impl(Ctx& c, int slot0, int n, const double* F, const double* U0) {
+  pmg_handle h = c.h;
+  pmg_ws ws = c.w;
+  const int N = h->dl[0].N, R = ws->R;
+  const DevPLevel& D = h->dl[0];
+  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, F, ws->bF);
+  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, U0, ws->bU);
+  ws->launches += 2;
+  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
+    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
+    pmgk::k_slots_start<<<1, 128, 0, c.s>>>(pmgk::kNormBlocks, R, slot0, n, ws->bpart, ws->br0, ws->brel,
+                                            ws->bmask, ws->bstate, ws->biters);
   });
+  for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 1;
+  PMG_CUDA(cudaGetLastError());
+  return PMG_OK;
 }
 
+// One cycle's work, stream-ordered (capturable: no host synchronisation).
+pmg_status slots_cycle_body(Ctx& c, int precision, double tol) {
+  pmg_handle h = c.h;
+  pmg_ws ws = c.w;
+  const int N = h->dl[0].N, R = ws->R;
+  const DevPLevel& D = h->dl[0];
+  pmg_status st = begin_launches(c);
+  if (st != PMG_OK) return st;
+  if (precision == PMG_PREC_MIXED) {
+    float* r32 = reinterpret_cast<float*>(ws->bf[0]);
+    float* e32 = reinterpret_cast<float*>(ws->be[0]);
+    b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
+    b_vcycle0<float>(c, 0, r32, e32);
+    pmgk::k_masked_update<float><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, e32, ws->bmask,
+                                                                                                 ws->bU);
+  } else {
+    b_vcycle0<double>(c, 0, ws->bR, ws->be[0]);
+    pmgk::k_masked_update<double><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, ws->be[0],
+                                                                                                  ws->bmask, ws->bU);
+  }
+  ++ws->launches;
+  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
+  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
+    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
+    pmgk::k_slots_update<<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, tol, ws->bpart, ws->br0, ws->brel,
+                                                           ws->bmask, ws->bstate, ws->biters);
+  });
+  PMG_CUDA(cudaMemcpyAsync(ws->hm.relres, ws->brel, R * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(ws->hm.state, ws->bstate, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(ws->hm.iters, ws->biters, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaMemcpyAsync(ws->hm.err, ws->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
+  PMG_CUDA(cudaGetLastError());
+  return PMG_OK;
+}
+
+// Enqueues one cycle.  On a non-default stream without profiling, the cycle
+// runs as a CUDA graph: the second call for a (precision, tolerance, kernel
+// choice) captures the launch sequence, later calls replay it with one launch
+// (the first call runs eagerly, which also sets every kernel's attributes
+// outside any capture).
+pmg_status slots_cycle_impl(Ctx& c, int precision, double tol) {
+  pmg_handle h = c.h;
+  pmg_ws ws = c.w;
+  auto& g = ws->cyc[precision == PMG_PREC_MIXED ? 1 : 0];
+  const bool graphable = ws->graphs && !ws->prof && c.s != nullptr;
+  pmg_status st = PMG_OK;
+  if (graphable && g.exec && (g.tol != tol || g.epoch != h->tune_epoch)) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.eager = 0;
+  }
+  if (graphable && !g.exec && g.eager >= 1) {
+    const long long l0 = ws->launches;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      st = slots_cycle_body(c, precision, tol);
+      const cudaError_t e = cudaStreamEndCapture(c.s, &graph);
+      if (st == PMG_OK && e == cudaSuccess && graph &&
+          cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess) {
+        g.tol = tol;
+        g.epoch = h->tune_epoch;
+        g.launches = ws->launches - l0;
+      } else {
+        g.exec = nullptr;
+        ws->graphs = false;            // capture refused here: stay eager on this workspace
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+    } else {
+      ws->graphs = false;
+      cudaGetLastError();
+    }
+    ws->launches = l0;
+    st = PMG_OK;
+  }
+  if (graphable && g.exec) {
+    PMG_CUDA(cudaGraphLaunch(g.exec, c.s));
+    ws->launches += g.launches;
+    ++ws->graph_launches;
+  } else {
+    if ((st = slots_cycle_body(c, precision, tol)) != PMG_OK) return st;
+    ++g.eager;
+  }
+  PMG_CUDA(cudaEventRecord(ws->slot_ev, c.s));
+  ws->slot_pending = true;
+  return PMG_OK;
+}
+
+pmg_status slots_wait_impl(pmg_ws ws, bool blocking, bool* ready) {
+  *ready = false;
+  if (!ws->slot_pending) { *ready = true; return PMG_OK; }
+  const cudaError_t q = blocking ? cudaEventSynchronize(ws->slot_ev) : cudaEventQuery(ws->slot_ev);
+  if (q == cudaErrorNotReady) return PMG_OK;
+  if (q != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(q));
+  ws->slot_pending = false;
+  *ready = true;
+  collect_profile(ws);
+  for (int k = 0; k < ws->R; ++k) ws->slot_state[k] = ws->hm.state[k];
+  if (ws->hm.err[0]) {
+    cudaMemset(ws->err, 0, 4 * sizeof(unsigned));
+    char buf[160];
+    std::snprintf(buf, sizeof(buf),
+                  "a device-side dependency wait expired (wait sites 0x%x; first: site 0x%x, item %u, row %u, warp %u)",
+                  ws->hm.err[0], ws->hm.err[1], ws->hm.err[2], ws->hm.err[3] >> 8, ws->hm.err[3] & 0xffu);
+    ws->hm.err[0] = 0;
+    return fail(PMG_ERR_TIMEOUT, buf);
+  }
+  return PMG_OK;
+}
+
+pmg_status slots_read_impl(Ctx& c, int slot0, int n, double* U) {
+  const int N = c.h->dl[0].N;
+  pmgk::k_slots_copy_out<<<grid_for((long long)N * n, 256, c.h->sms * 16), 256, 0, c.s>>>(N, n, c.w->R, slot0,
+                                                                                           c.w->bU, U);
+  ++c.w->launches;
+  PMG_CUDA(cudaGetLastError());
+  return PMG_OK;
+}
+
+pmg_status slots_release_impl(Ctx& c, int slot0, int n) {
+  pmgk::k_slots_release<<<1, 128, 0, c.s>>>(c.w->R, slot0, n, c.w->bmask, c.w->bstate);
+  ++c.w->launches;
+  PMG_CUDA(cudaGetLastError());
+  for (int k = slot0; k < slot0 + n; ++k) c.w->slot_state[k] = 0;
+  return PMG_OK;
+}
+
+// pmg_solve_batched: all right-hand sides in slots 0..nrhs-1, cycles until
+// none is active.
 pmg_status solve_batched_impl(pmg_handle h, pmg_ws ws, int nrhs, const double* F, const double* U0, double tol,
                               int max_iter, int precision, double* Uout, int* iters, double* hist,
                               cudaStream_t s) {
   Ctx c{h, ws, s};
-  const int N = h->dl[0].N, R = ws->R;
-  const DevPLevel& D = h->dl[0];
-  std::vector<double> r0(R), rel(R), mask(R, 0.0);
-  std::vector<int> done(nrhs, 0);
+  bool ready = false;
+  pmg_status st = slots_wait_impl(ws, true, &ready);
+  if (st != PMG_OK) return st;
+  if ((st = slots_release_impl(c, 0, ws->max_rhs)) != PMG_OK) return st;
+  if ((st = slots_load_impl(c, 0, nrhs, F, U0)) != PMG_OK) return st;
   for (int k = 0; k < nrhs; ++k) iters[k] = 0;
-  pmg_status st = begin_launches(c);
-  if (st != PMG_OK) return st;
-  pmgk::k_to_rows<<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, F, ws->bF);
-  pmgk::k_to_rows<<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, U0, ws->bU);
-  ws->launches += 2;
-  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
-  b_norms(c, N, ws->bR, 0);
-  PMG_CUDA(cudaMemcpyAsync(r0.data(), ws->br0, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-  st = finish_launches(c);
-  if (st != PMG_OK) return st;
-  int active = 0;
-  for (int k = 0; k < nrhs; ++k) {
-    if (r0[k] > 0.0) { mask[k] = 1.0; ++active; } else done[k] = 1;
+  for (int it = 0; it < max_iter; ++it) {
+    if (std::find(ws->slot_state.begin(), ws->slot_state.begin() + nrhs, 1) == ws->slot_state.begin() + nrhs) break;
+    if ((st = slots_cycle_impl(c, precision, tol)) != PMG_OK) return st;
+    if ((st = slots_wait_impl(ws, true, &ready)) != PMG_OK) return st;
+    for (int k = 0; k < nrhs; ++k) {
+      if (ws->hm.iters[k] != it + 1) continue;        // not active in this cycle
+      iters[k] = it + 1;
+      if (hist) hist[(size_t)it * nrhs + k] = ws->hm.relres[k];
+    }
   }
   pmg_status result = PMG_OK;
-  for (int it = 0; it < max_iter && active > 0; ++it) {
-    st = begin_launches(c);
-    if (st != PMG_OK) return st;
-    PMG_CUDA(cudaMemcpyAsync(ws->bmask, mask.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
-    if (precision == PMG_PREC_MIXED) {
-      float* r32 = reinterpret_cast<float*>(ws->bf[0]);
-      float* e32 = reinterpret_cast<float*>(ws->be[0]);
-      b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
-      b_vcycle0<float>(c, 0, r32, e32);
-      pmgk::k_masked_update<float><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, R, e32, ws->bmask, ws->bU);
-    } else {
-      double* e64 = ws->be[0];
-      b_vcycle0<double>(c, 0, ws->bR, e64);
-      pmgk::k_masked_update<double><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, s>>>(N, R, e64, ws->bmask, ws->bU);
-    }
-    ++ws->launches;
-    b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
-    b_norms(c, N, ws->bR, 1);
-    PMG_CUDA(cudaMemcpyAsync(rel.data(), ws->brel, R * sizeof(double), cudaMemcpyDeviceToHost, s));
-    st = finish_launches(c);
-    if (st != PMG_OK) return st;
-    for (int k = 0; k < nrhs; ++k) {
-      if (done[k]) continue;
-      if (hist) hist[(size_t)it * nrhs + k] = rel[k];
-      iters[k] = it + 1;
-      if (rel[k] < tol) { done[k] = 1; mask[k] = 0.0; --active; }
-      else if (!(rel[k] <= 1e10)) { done[k] = 1; mask[k] = 0.0; --active; result = PMG_ERR_DIVERGED; }
-    }
+  for (int k = 0; k < nrhs; ++k) {
+    if (ws->slot_state[k] == 3) result = PMG_ERR_DIVERGED;
+    else if (ws->slot_state[k] == 1 && result == PMG_OK) result = PMG_ERR_MAXITER;
   }
-  if (active > 0 && result == PMG_OK) { result = PMG_ERR_MAXITER; g_last_error = "maximum number of V-cycles reached"; }
+  if (result == PMG_ERR_MAXITER) g_last_error = "maximum number of V-cycles reached";
   if (result == PMG_ERR_DIVERGED) g_last_error = "relative residual exceeded 1e10 for a right-hand side";
-  pmgk::k_from_rows<<<grid_for((long long)N * nrhs, 256, h->sms * 16), 256, 0, s>>>(N, nrhs, R, ws->bU, Uout);
-  ++ws->launches;
-  PMG_CUDA(cudaGetLastError());
+  if ((st = slots_read_impl(c, 0, nrhs, Uout)) != PMG_OK) return st;
+  if ((st = slots_release_impl(c, 0, ws->max_rhs)) != PMG_OK) return st;
   PMG_CUDA(cudaStreamSynchronize(s));
   return result;
-}
-
-// Continuous batching: end of every slot operation.  The per-slot relative
-// residual, state and iteration count and the error words are copied into
-// the workspace's pinned mirror and an event marks the point; pmg_slots_wait
-// reads the mirror once the event has passed.
-pmg_status slots_snapshot(Ctx& c) {
-  pmg_ws w = c.w;
-  const int R = w->R;
-  PMG_CUDA(cudaMemcpyAsync(w->hm.relres, w->brel, R * sizeof(double), cudaMemcpyDeviceToHost, c.s));
-  PMG_CUDA(cudaMemcpyAsync(w->hm.state, w->bstate, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
-  PMG_CUDA(cudaMemcpyAsync(w->hm.iters, w->biters, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
-  PMG_CUDA(cudaMemcpyAsync(w->hm.err, w->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
-  PMG_CUDA(cudaEventRecord(w->slot_ev, c.s));
-  PMG_CUDA(cudaGetLastError());
-  w->slot_pending = true;
-  return PMG_OK;
 }
 
 pmg_status slots_check(pmg_handle h, pmg_ws ws) {
@@ -1331,24 +1440,11 @@ pmg_status pmg_slots_load(pmg_handle h, pmg_ws ws, int slot0, int n, const doubl
   pmg_status st = slots_check(h, ws);
   if (st != PMG_OK) return st;
   if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs || !F || !U0) return fail(PMG_ERR_ARG, "invalid slot range");
-  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a cycle is pending: call pmg_slots_wait first");
   for (int k = slot0; k < slot0 + n; ++k)
     if (ws->slot_state[k] == 1) return fail(PMG_ERR_BUSY, "slot " + std::to_string(k) + " is active");
   Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
-  const int N = h->dl[0].N, R = ws->R;
-  const DevPLevel& D = h->dl[0];
-  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, F, ws->bF);
-  pmgk::k_slots_copy_in<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, c.s>>>(N, n, R, slot0, U0, ws->bU);
-  ws->launches += 2;
-  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
-  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
-    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
-    pmgk::k_slots_start<<<1, 128, 0, c.s>>>(pmgk::kNormBlocks, R, slot0, n, ws->bpart, ws->br0, ws->brel,
-                                            ws->bmask, ws->bstate, ws->biters);
-  });
-  for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 1;
-  PMG_CUDA(cudaGetLastError());
-  return PMG_OK;
+  return slots_load_impl(c, slot0, n, F, U0);
 }
 
 pmg_status pmg_slots_cycle(pmg_handle h, pmg_ws ws, int precision, double rel_tol, void* stream) {
@@ -1356,56 +1452,20 @@ pmg_status pmg_slots_cycle(pmg_handle h, pmg_ws ws, int precision, double rel_to
   if (st != PMG_OK) return st;
   if (!(rel_tol > 0) || (precision != PMG_PREC_FP64 && precision != PMG_PREC_MIXED))
     return fail(PMG_ERR_ARG, "invalid cycle argument");
-  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a cycle is pending: call pmg_slots_wait first");
   if (std::find(ws->slot_state.begin(), ws->slot_state.end(), 1) == ws->slot_state.end()) return PMG_OK;
   Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
-  const int N = h->dl[0].N, R = ws->R;
-  const DevPLevel& D = h->dl[0];
-  if ((st = begin_launches(c)) != PMG_OK) return st;
-  if (precision == PMG_PREC_MIXED) {
-    float* r32 = reinterpret_cast<float*>(ws->bf[0]);
-    float* e32 = reinterpret_cast<float*>(ws->be[0]);
-    b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
-    b_vcycle0<float>(c, 0, r32, e32);
-    pmgk::k_masked_update<float><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, e32, ws->bmask,
-                                                                                                 ws->bU);
-  } else {
-    b_vcycle0<double>(c, 0, ws->bR, ws->be[0]);
-    pmgk::k_masked_update<double><<<grid_for((long long)N * R, 256, h->sms * 16), 256, 0, c.s>>>(N, R, ws->be[0],
-                                                                                                  ws->bmask, ws->bU);
-  }
-  ++ws->launches;
-  b_spmm<double, double, double, 0>(c, PMG_K_RESIDUAL, as_t(D.A), D.nnzA, ws->bU, ws->bF, ws->bR);
-  launch(c, PMG_K_NORM, 8.0 * N * R, [&] {
-    pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
-    pmgk::k_slots_update<<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, rel_tol, ws->bpart, ws->br0,
-                                                           ws->brel, ws->bmask, ws->bstate, ws->biters);
-  });
-  return slots_snapshot(c);
+  return slots_cycle_impl(c, precision, rel_tol);
 }
 
 pmg_status pmg_slots_wait(pmg_handle h, pmg_ws ws, int blocking, int* ready, double* relres, int* state, int* iters) {
   pmg_status st = slots_check(h, ws);
   if (st != PMG_OK) return st;
   if (!ready) return fail(PMG_ERR_ARG, "ready is NULL");
-  *ready = 0;
-  if (ws->slot_pending) {
-    const cudaError_t q = blocking ? cudaEventSynchronize(ws->slot_ev) : cudaEventQuery(ws->slot_ev);
-    if (q == cudaErrorNotReady) return PMG_OK;
-    if (q != cudaSuccess) return fail(PMG_ERR_CUDA, cudaGetErrorString(q));
-    ws->slot_pending = false;
-    collect_profile(ws);
-    for (int k = 0; k < ws->R; ++k) ws->slot_state[k] = ws->hm.state[k];
-    if (ws->hm.err[0]) {
-      cudaMemset(ws->err, 0, 4 * sizeof(unsigned));
-      char buf[160];
-      std::snprintf(buf, sizeof(buf),
-                    "a device-side dependency wait expired (wait sites 0x%x; first: site 0x%x, item %u, row %u, warp %u)",
-                    ws->hm.err[0], ws->hm.err[1], ws->hm.err[2], ws->hm.err[3] >> 8, ws->hm.err[3] & 0xffu);
-      return fail(PMG_ERR_TIMEOUT, buf);
-    }
-  }
-  *ready = 1;
+  bool r = false;
+  st = slots_wait_impl(ws, blocking != 0, &r);
+  *ready = r ? 1 : 0;
+  if (st != PMG_OK || !r) return st;
   for (int k = 0; k < ws->max_rhs; ++k) {
     if (relres) relres[k] = ws->hm.relres[k];
     if (state) state[k] = ws->slot_state[k];
@@ -1418,24 +1478,17 @@ pmg_status pmg_slots_read(pmg_handle h, pmg_ws ws, int slot0, int n, double* U, 
   pmg_status st = slots_check(h, ws);
   if (st != PMG_OK) return st;
   if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs || !U) return fail(PMG_ERR_ARG, "invalid slot range");
-  const int N = h->dl[0].N;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  pmgk::k_slots_copy_out<<<grid_for((long long)N * n, 256, h->sms * 16), 256, 0, s>>>(N, n, ws->R, slot0, ws->bU, U);
-  ++ws->launches;
-  PMG_CUDA(cudaGetLastError());
-  return PMG_OK;
+  Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
+  return slots_read_impl(c, slot0, n, U);
 }
 
 pmg_status pmg_slots_release(pmg_handle h, pmg_ws ws, int slot0, int n, void* stream) {
   pmg_status st = slots_check(h, ws);
   if (st != PMG_OK) return st;
   if (slot0 < 0 || n < 1 || slot0 + n > ws->max_rhs) return fail(PMG_ERR_ARG, "invalid slot range");
-  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a slot operation is pending: call pmg_slots_wait first");
-  pmgk::k_slots_release<<<1, 128, 0, static_cast<cudaStream_t>(stream)>>>(ws->R, slot0, n, ws->bmask, ws->bstate);
-  ++ws->launches;
-  PMG_CUDA(cudaGetLastError());
-  for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 0;
-  return PMG_OK;
+  if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a cycle is pending: call pmg_slots_wait first");
+  Ctx c{h, ws, static_cast<cudaStream_t>(stream)};
+  return slots_release_impl(c, slot0, n);
 }
 
 pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
@@ -1523,6 +1576,7 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ws->prof = prof;
+  ++h->tune_epoch;
   return err;
 }
 
@@ -1553,6 +1607,7 @@ pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
     HTune& t = h->htune[j];
     t.gF = field(v, 0); t.gB = field(v, 1); t.bF = field(v, 2); t.bB = field(v, 3);
   }
+  ++h->tune_epoch;
   return PMG_OK;
 }
 
@@ -1695,9 +1750,11 @@ pmg_status pmg_ws_stats(pmg_ws ws, pmg_stats_t* out, int reset) {
     out->bytes[k] = ws->prof_bytes[k];
   }
   out->total_launches = ws->launches;
+  out->graph_launches = ws->graph_launches;
   if (reset) {
     for (int k = 0; k < PMG_NKERN; ++k) { ws->prof_ms[k] = 0; ws->prof_n[k] = 0; ws->prof_bytes[k] = 0; }
     ws->launches = 0;
+    ws->graph_launches = 0;
   }
   return PMG_OK;
 }

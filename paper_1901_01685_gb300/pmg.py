@@ -79,10 +79,11 @@ class pmg_info_t(C.Structure):
 
 class pmg_stats_t(C.Structure):
     _fields_ = [("ms", C.c_double * PMG_NKERN), ("launches", C.c_longlong * PMG_NKERN),
-                ("bytes", C.c_double * PMG_NKERN), ("total_launches", C.c_longlong)]
+                ("bytes", C.c_double * PMG_NKERN), ("total_launches", C.c_longlong),
+                ("graph_launches", C.c_longlong)]
 
     def as_dict(self) -> dict:
-        return {"total_launches": self.total_launches,
+        return {"total_launches": self.total_launches, "graph_launches": self.graph_launches,
                 "per_class": {KERNEL_CLASSES[k]: {"ms": self.ms[k], "launches": self.launches[k],
                                                    "bytes": self.bytes[k]} for k in range(PMG_NKERN)}}
 

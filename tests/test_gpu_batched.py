@@ -187,3 +187,27 @@ def test_batched_repeated_solves_are_bit_identical(torch_mod, pmg, oracle_mod):
             U, it, h, st = S.solve_batched(Fd, U0d, precision=prec)
             assert st == 0 and np.array_equal(it, it0) and np.array_equal(h, h0)
             assert torch.equal(U, ref)
+
+
+def test_graph_replayed_cycles_match_eager_cycles(torch_mod, pmg, oracle_mod):
+    """On a non-default stream the batched cycles run as captured CUDA graphs;
+    the results equal the eagerly launched cycles of the default stream bit
+    for bit, and the replays are counted."""
+    torch = torch_mod
+    S = pmg.Solver(0, 3, 6, max_rhs=40)
+    F = inputs.batched_rhs(S.rhs(), 40, seed=17)
+    U0 = np.stack([inputs.initial_guess(S.N, 700 + r) for r in range(40)])
+    Fd, U0d = _dev(torch, F), _dev(torch, U0)
+    side = torch.cuda.Stream()
+    for prec in (pmg.PMG_PREC_FP64, pmg.PMG_PREC_MIXED):
+        Ue, ite, he, _ = S.solve_batched(Fd, U0d, precision=prec)
+        Ue = Ue.clone()
+        pmg.pmg_ws_stats(S.ws, reset=True)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):                  # first solve: eager, capture, replays; second: replays only
+                Ug, itg, hg, st = S.solve_batched(Fd, U0d, precision=prec)
+                torch.cuda.current_stream().synchronize()
+                assert st == 0 and np.array_equal(itg, ite) and np.array_equal(hg, he)
+                assert torch.equal(Ug, Ue)
+        assert pmg.pmg_ws_stats(S.ws).graph_launches >= 2 * int(ite.max()) - 2
