@@ -110,6 +110,7 @@ struct DevPLevel {
   pmgk::LpB<float> Lb32{}, Ub32{};
   pmgk::LpC<double> Lc64{}, Uc64{};   // ring kernel layouts (U mirrored)
   pmgk::LpC<float> Lc32{}, Uc32{};
+  int inflightL = 0, inflightU = 0;    // lines of one group the solve's pipeline keeps busy at once
 };
 // Kernel variant of each solve: the line-pipelined windowed kernel (single
 // vectors), the ring kernel, or the lines-per-CTA kernel (batched).  Defaults
@@ -134,6 +135,7 @@ struct DevHLevel {
   double avg_lo = 0, avg_up = 0;
   pmgk::LpB<double> Lob{}, UpMb{};   // batched Gauss-Seidel layouts
   pmgk::LpC<double> Loc{}, UpMc{};
+  int inflightGS = 0;
 };
 
 }  // namespace
@@ -308,6 +310,16 @@ void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, doub
   }
 }
 
+// Lines of one right-hand-side group that a line-pipelined solve keeps busy at
+// once: with a critical path of `depth` rows over `nlines` lines of nx rows,
+// consecutive lines lag by about (depth - nx) / (nlines - 1) rows, so about
+// nx / lag lines are between their first and last row at any time (+4 slack).
+int lines_in_flight(int depth, int nx, int nlines) {
+  if (nlines <= 1) return 1;
+  const int lag = std::max(1, (depth - nx) / (nlines - 1));
+  return std::min(nlines, nx / lag + 4);
+}
+
 // Raises a kernel's dynamic shared-memory limit to kLpSmemCap once per device.
 void allow_smem(const void* fn) {
   static std::mutex mu;
@@ -422,7 +434,8 @@ bool lp_launch(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double*
 
 // Ring-kernel batched solve; false when the line does not fit in shared memory.
 template <class T>
-bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0) {
+bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0,
+           int inflight = 0) {
   const size_t smem = size_t(M.nx + 64) * 32 * sizeof(T);
   if (smem > kLpSmemCap) return false;
   const int R = nrhs > 0 ? nrhs : c.w->R, threads = 32 * (1 + pmgk::LpcProducers<T>::value);
@@ -446,8 +459,14 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, c
   allow_smem(fn);
   int occ = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
-  const int nitems = M.nlines * std::max(1, R / 32);
-  const int grid = std::max(1, std::min(nitems, c.h->sms * occ));
+  // Only about `inflight` lines per group can make progress at once (the
+  // pipeline's lag); more CTAs would only poll, taking issue slots and L2
+  // bandwidth from the working ones (and from other streams' kernels).
+  const int groups = std::max(1, R / 32);
+  const int nitems = M.nlines * groups;
+  int grid = std::min(nitems, c.h->sms * occ);
+  if (inflight > 0) grid = std::min(grid, inflight * groups);
+  grid = std::max(1, grid);
   unsigned* cnt = next_counter(c);
   launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
     cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
@@ -469,7 +488,8 @@ void b_axpy(Ctx& c, int cls, long long n, const T* x, T* y) {
 
 void lsolve(Ctx& c, int l, const double* b, double* y) {
   const DevPLevel& D = c.h->dl[l];
-  if (c.h->ptune[l].sL == kVarRing && b_lpc<double>(c, PMG_K_LSOLVE, D.Lc64, D.nnzL, false, b, y, 1)) return;
+  if (c.h->ptune[l].sL == kVarRing && b_lpc<double>(c, PMG_K_LSOLVE, D.Lc64, D.nnzL, false, b, y, 1, D.inflightL))
+    return;
   launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
     if (lp_launch(c, D.Llp, false, b, y, nullptr)) return;
     const unsigned ep = next_epoch(c);
@@ -479,7 +499,7 @@ void lsolve(Ctx& c, int l, const double* b, double* y) {
 }
 void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
   const DevPLevel& D = c.h->dl[l];
-  if (c.h->ptune[l].sU == kVarRing && b_lpc<double>(c, PMG_K_USOLVE, D.Uc64, D.nnzU, true, y, e, 1)) {
+  if (c.h->ptune[l].sU == kVarRing && b_lpc<double>(c, PMG_K_USOLVE, D.Uc64, D.nnzU, true, y, e, 1, D.inflightU)) {
     if (u) b_axpy<double>(c, PMG_K_USOLVE, D.N, e, u);
     return;
   }
@@ -513,7 +533,7 @@ void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   if (var == kVarRing && size_t(ring.nx + 64) * 32 * sizeof(double) <= kLpSmemCap) {
     launch(c, PMG_K_GS, csr_bytes(D.nnzA / 2, D.N) + 24.0 * D.N,
            [&] { spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms); });
-    b_lpc<double>(c, PMG_K_GS, ring, D.nnzA / 2, backward, t, xn, 1);
+    b_lpc<double>(c, PMG_K_GS, ring, D.nnzA / 2, backward, t, xn, 1, D.inflightGS);
     cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
     return;
   }
@@ -748,7 +768,8 @@ void b_gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   if (backward) b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Lo), D.nnzA / 2, x, b, t);
   else b_spmm<double, double, double, 0>(c, PMG_K_GS, as_t(D.Up), D.nnzA / 2, x, b, t);
   const unsigned char var = backward ? c.h->htune[j].bB : c.h->htune[j].bF;
-  if (var != kVarRing || !b_lpc<double>(c, PMG_K_GS, backward ? D.UpMc : D.Loc, D.nnzA / 2, backward, t, xn))
+  if (var != kVarRing ||
+      !b_lpc<double>(c, PMG_K_GS, backward ? D.UpMc : D.Loc, D.nnzA / 2, backward, t, xn, 0, D.inflightGS))
     b_lp<double>(c, PMG_K_GS, backward ? D.UpMb : D.Lob, D.nnzA / 2, backward, t, xn, nullptr);
   cudaMemcpyAsync(x, xn, size_t(D.N) * R * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
 }
@@ -783,11 +804,12 @@ void b_tri(Ctx& c, int l, bool upper, unsigned char var, const T* b, T* x) {
   const DevPLevel& D = c.h->dl[l];
   const int cls = upper ? PMG_K_USOLVE : PMG_K_LSOLVE;
   const long long nnz = upper ? D.nnzU : D.nnzL;
+  const int infl = upper ? D.inflightU : D.inflightL;
   if constexpr (sizeof(T) == 4) {
-    if (var == kVarRing && b_lpc<float>(c, cls, upper ? D.Uc32 : D.Lc32, nnz, upper, b, x)) return;
+    if (var == kVarRing && b_lpc<float>(c, cls, upper ? D.Uc32 : D.Lc32, nnz, upper, b, x, 0, infl)) return;
     b_lp<float>(c, cls, upper ? D.Ub32 : D.Lb32, nnz, upper, b, x, nullptr);
   } else {
-    if (var == kVarRing && b_lpc<double>(c, cls, upper ? D.Uc64 : D.Lc64, nnz, upper, b, x)) return;
+    if (var == kVarRing && b_lpc<double>(c, cls, upper ? D.Uc64 : D.Lc64, nnz, upper, b, x, 0, infl)) return;
     b_lp<double>(c, cls, upper ? D.Ub64 : D.Lb64, nnz, upper, b, x, nullptr);
   }
 }
@@ -1277,6 +1299,8 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
       const auto& cu32 = h->coffU32[l];
       const pmgk::Csr FL = bind(cl.far, base), FU = bind(cu.far, base);
       const pmgk::Csr FL32 = bind(cl32.far, base), FU32 = bind(cu32.far, base);
+      D.inflightL = lines_in_flight(h->H.lev[l].depthL, nx, D.N / nx);
+      D.inflightU = lines_in_flight(h->H.lev[l].depthU, nx, D.N / nx);
       D.Lc64 = pmgk::LpC<double>{D.N, nx, D.N / nx, cl.ring, FL.rp, FL.ci, FL.v, D.Llp.push, nullptr};
       D.Uc64 = pmgk::LpC<double>{D.N, nx, D.N / nx, cu.ring, FU.rp, FU.ci, FU.v, D.Ulp.push, D.Ulp.dscale};
       D.Lc32 = pmgk::LpC<float>{D.N, nx, D.N / nx, cl32.ring, FL32.rp, FL32.ci, fp(cl32.far32), fp(cl32.push32),
@@ -1303,6 +1327,7 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
       D.Lob = pmgk::LpB<double>{D.N, nx, D.N / nx, D.Lo.rp, D.Lo.ci, D.Lo.v, D.dinv};
       D.UpMb = pmgk::LpB<double>{D.N, nx, D.N / nx, UpM.rp, UpM.ci, UpM.v,
                                  reinterpret_cast<const double*>(base + h->hboff[j].dinvM)};
+      D.inflightGS = lines_in_flight(h->H.hl[j].depthGS, nx, D.N / nx);
       const pmgk::Csr FLo = bind(h->coffLo[j].far, base), FUp = bind(h->coffUpM[j].far, base);
       D.Loc = pmgk::LpC<double>{D.N, nx, D.N / nx, h->coffLo[j].ring, FLo.rp, FLo.ci, FLo.v, D.Lolp.push,
                                 D.Lolp.dscale};
