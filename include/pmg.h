@@ -157,8 +157,10 @@ pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const d
                           double rel_tol, int max_iter, double* u_host, int* iters,
                           double* hist_host, int hist_cap, void* stream);
 
-/* Precision of the batched solve's inner V-cycle. */
-enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1 };
+/* Precision of the batched solve's inner V-cycle: FP64; FP32 arithmetic with
+ * FP32 factors; FP32 arithmetic with the ILUT factors' values stored as FP16
+ * or as BF16 (widened to FP32 on load). */
+enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_FP16 = 2, PMG_PREC_MIXED_BF16 = 3 };
 
 /* Batched stand-alone solves of nrhs right-hand sides with one hierarchy.
  * Each right-hand side follows the iteration u <- u + C(f - A u) of Sec. 5, C

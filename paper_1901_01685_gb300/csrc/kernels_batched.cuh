@@ -6,6 +6,8 @@
 // warp (broadcast loads) and vector accesses are coalesced.  Value type T is
 // double (plain FP64) or float (the inner cycle of FP64 defect correction).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
@@ -243,16 +245,23 @@ struct LpcProducers { static constexpr int value = 8; };
 static_assert(32 % LpcProducers<float>::value == 0 && 32 % LpcProducers<double>::value == 0,
               "producer count must divide the 32 hand-over slots");
 
-template <class T>
+// CT: storage type of the factor coefficients (T, or FP16 / BF16 with T = float:
+// stored at 16 bits, widened on load, accumulated in T).
+template <class T, class CT = T>
 struct LpC {
   int n, nx, nlines;
   int ring;           // ring width: own-line entries at distance 1..ring-1 are pushed
   const int* frp;
   const int* fci;
-  const T* fv;        // far entries, values scaled by d_i
-  const T* push;      // [n][32]: push[j*32 + k-1] = c_{j,k}
+  const CT* fv;       // far entries, values scaled by d_i
+  const CT* push;     // [n][32]: push[j*32 + k-1] = c_{j,k}
   const T* dscale;    // d_i, or null when d = 1
 };
+
+__device__ __forceinline__ float coef_ld(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double coef_ld(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float coef_ld(const __half* p) { return __half2float(__ldg(p)); }
+__device__ __forceinline__ float coef_ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 
 // The first NC coefficients of a hand-over row in shared memory (16-byte aligned).
 template <int NC>
@@ -285,8 +294,8 @@ __device__ __forceinline__ T lpc_wait_filled(volatile T* p, unsigned* err, unsig
   return lpb_wait<T, true>(const_cast<const T*>(p), err, site, item, row);
 }
 
-template <class T, bool MIRROR, int RING>
-__global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T> M, int R, const T* __restrict__ b, T* x,
+template <class T, bool MIRROR, int RING, class CT = T>
+__global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T, CT> M, int R, const T* __restrict__ b, T* x,
                                                                    unsigned* counter, unsigned* err) {
   static_assert(RING >= 2 && RING <= 32 && (RING & (RING - 1)) == 0, "ring must be a power of two <= 32");
   constexpr int NC = RING - 1;
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
         const int i = row0 + ix;
         const size_t o = (size_t)lp_vec<MIRROR>(i, M.n) * R + col;
         const T bi = M.dscale ? b[o] * __ldg(M.dscale + i) : b[o];
-        const T cf = lane < NC ? __ldg(M.push + (size_t)i * 32 + lane) : T(0);
+        const T cf = lane < NC ? (T)coef_ld(M.push + (size_t)i * 32 + lane) : T(0);
         const int beg = __ldg(M.frp + i), end = __ldg(M.frp + i + 1);
         T a[4] = {T(0), T(0), T(0), T(0)};
         for (int t0 = beg; t0 < end; t0 += BATCH) {
@@ -356,7 +365,7 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
           for (int q = 0; q < BATCH; ++q) {
             const int t = t0 + q;
             jj[q] = t < end ? __ldg(M.fci + t) : -1;
-            cv[q] = t < end ? __ldg(M.fv + t) : T(0);
+            cv[q] = t < end ? (T)coef_ld(M.fv + t) : T(0);
           }
           // Issue every load of the batch first, then resolve the pending ones
           // (own line from shared memory, earlier lines with relaxed loads at

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -110,6 +111,8 @@ struct DevPLevel {
   pmgk::LpB<float> Lb32{}, Ub32{};
   pmgk::LpC<double> Lc64{}, Uc64{};   // ring kernel layouts (U mirrored)
   pmgk::LpC<float> Lc32{}, Uc32{};
+  pmgk::LpC<float, __half> Lc16{}, Uc16{};           // FP16 / BF16 factor storage, FP32 arithmetic
+  pmgk::LpC<float, __nv_bfloat16> Lcb{}, Ucb{};
   int inflightL = 0, inflightU = 0;    // lines of one group the solve's pipeline keeps busy at once
 };
 // Kernel variant of each solve: the line-pipelined windowed kernel (single
@@ -156,7 +159,8 @@ struct pmg_hierarchy_s {
   std::vector<HBOff> hboff;
   // ring kernel layouts: far parts (FP64 CSR + FP32 values), FP32 push rings and scales
   std::vector<pmgl::Csr> farstore;
-  struct COff { DevCsrOff far; int ring; size_t far32, push32, d32; };
+  struct COff { DevCsrOff far; int ring; size_t far32, push32, d32, far16, push16, farb, pushb; };
+  std::vector<std::vector<uint16_t>> h16store;     // FP16 / BF16 bit patterns of the factors
   std::vector<COff> coffL, coffU, coffL32, coffU32, coffLo, coffUpM;
   size_t off_cinv = 0;
   bool uploaded = false;
@@ -194,7 +198,7 @@ struct pmg_workspace_s {
   bool slot_pending = false;
   // CUDA-graph replay of the slot cycle, per precision
   struct CycleGraph { cudaGraphExec_t exec = nullptr; double tol = 0; unsigned epoch = 0; long long launches = 0; int eager = 0; };
-  CycleGraph cyc[2];
+  CycleGraph cyc[4];
   bool graphs = true;
   long long graph_launches = 0;
   unsigned* flags = nullptr;
@@ -334,6 +338,7 @@ struct Ctx {
   pmg_hierarchy_s* h;
   pmg_ws w;
   cudaStream_t s;
+  int fstore = 0;       // FP32 inner cycle: factor storage 0 FP32, 1 FP16, 2 BF16
 };
 
 cudaEvent_t pool_event(pmg_ws w) {
@@ -433,15 +438,15 @@ bool lp_launch(Ctx& c, const pmgk::Lp2& M, bool mirror, const double* b, double*
 }
 
 // Ring-kernel batched solve; false when the line does not fit in shared memory.
-template <class T>
-bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0,
+template <class T, class CT = T>
+bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T, CT>& M, long long nnz, bool mirror, const T* b, T* x, int nrhs = 0,
            int inflight = 0) {
   const size_t smem = size_t(M.nx + 64) * 32 * sizeof(T);
   if (smem > kLpSmemCap) return false;
   const int R = nrhs > 0 ? nrhs : c.w->R, threads = 32 * (1 + pmgk::LpcProducers<T>::value);
   const void* fn = nullptr;
   auto pick = [&](auto mir, auto ring) {
-    fn = (const void*)pmgk::k_lpc<T, decltype(mir)::value, decltype(ring)::value>;
+    fn = (const void*)pmgk::k_lpc<T, decltype(mir)::value, decltype(ring)::value, CT>;
   };
   using F_ = std::false_type;
   using T_ = std::true_type;
@@ -449,8 +454,12 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, c
   using R16 = std::integral_constant<int, 16>;
   using R32 = std::integral_constant<int, 32>;
   switch (M.ring) {
-    case 2: mirror ? pick(T_{}, R2{}) : pick(F_{}, R2{}); break;
-    case 16: mirror ? pick(T_{}, R16{}) : pick(F_{}, R16{}); break;
+    case 2:
+      if constexpr (sizeof(CT) == sizeof(T)) { mirror ? pick(T_{}, R2{}) : pick(F_{}, R2{}); break; }
+      return false;   // 16-bit storage only for the ILUT factors
+    case 16:
+      if constexpr (sizeof(CT) == sizeof(T)) { mirror ? pick(T_{}, R16{}) : pick(F_{}, R16{}); break; }
+      return false;
     case 32:
       if constexpr (sizeof(T) == 4) { mirror ? pick(T_{}, R32{}) : pick(F_{}, R32{}); break; }
       return false;   // FP64 chains use narrower rings
@@ -470,7 +479,7 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T>& M, long long nnz, bool mirror, c
   unsigned* cnt = next_counter(c);
   launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
     cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
-    pmgk::LpC<T> m = M;
+    pmgk::LpC<T, CT> m = M;
     int r = R;
     const T* bb = b;
     void* args[] = {&m, &r, &bb, &x, &cnt, &c.w->err};
@@ -806,6 +815,9 @@ void b_tri(Ctx& c, int l, bool upper, unsigned char var, const T* b, T* x) {
   const long long nnz = upper ? D.nnzU : D.nnzL;
   const int infl = upper ? D.inflightU : D.inflightL;
   if constexpr (sizeof(T) == 4) {
+    if (c.fstore == 1 && b_lpc<float, __half>(c, cls, upper ? D.Uc16 : D.Lc16, nnz, upper, b, x, 0, infl)) return;
+    if (c.fstore == 2 && b_lpc<float, __nv_bfloat16>(c, cls, upper ? D.Ucb : D.Lcb, nnz, upper, b, x, 0, infl))
+      return;
     if (var == kVarRing && b_lpc<float>(c, cls, upper ? D.Uc32 : D.Lc32, nnz, upper, b, x, 0, infl)) return;
     b_lp<float>(c, cls, upper ? D.Ub32 : D.Lb32, nnz, upper, b, x, nullptr);
   } else {
@@ -910,7 +922,8 @@ pmg_status slots_cycle_body(Ctx& c, int precision, double tol) {
   const DevPLevel& D = h->dl[0];
   pmg_status st = begin_launches(c);
   if (st != PMG_OK) return st;
-  if (precision == PMG_PREC_MIXED) {
+  if (precision != PMG_PREC_FP64) {
+    c.fstore = precision == PMG_PREC_MIXED_FP16 ? 1 : precision == PMG_PREC_MIXED_BF16 ? 2 : 0;
     float* r32 = reinterpret_cast<float*>(ws->bf[0]);
     float* e32 = reinterpret_cast<float*>(ws->be[0]);
     b_cast<double, float>(c, (long long)N * R, ws->bR, r32);
@@ -945,7 +958,7 @@ pmg_status slots_cycle_body(Ctx& c, int precision, double tol) {
 pmg_status slots_cycle_impl(Ctx& c, int precision, double tol) {
   pmg_handle h = c.h;
   pmg_ws ws = c.w;
-  auto& g = ws->cyc[precision == PMG_PREC_MIXED ? 1 : 0];
+  auto& g = ws->cyc[precision];
   const bool graphable = ws->graphs && !ws->prof && c.s != nullptr;
   pmg_status st = PMG_OK;
   if (graphable && g.exec && (g.tol != tol || g.epoch != h->tune_epoch)) {
@@ -1159,6 +1172,17 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
   // Ring widths: FP32 chains push 31 values a row (one FMA each, cheap);
   // FP64 FMAs are slow on this part, so FP64 ILUT chains push 15 and the P1
   // sweeps (own-line entries at distance 1 only) push 1.
+  // 16-bit copies (round to nearest even) of the FP32 ring layouts' values
+  h->h16store.reserve(8 * h->H.lev.size());
+  auto h16 = [&](const std::vector<double>& v, bool bf16) {
+    h->h16store.emplace_back(v.size());
+    auto& w = h->h16store.back();
+    for (size_t i = 0; i < v.size(); ++i) {
+      if (bf16) { const __nv_bfloat16 q = __float2bfloat16_rn(float(v[i])); std::memcpy(&w[i], &q, 2); }
+      else { const __half q = __float2half_rn(float(v[i])); std::memcpy(&w[i], &q, 2); }
+    }
+    return P.add(w.data(), w.size() * sizeof(uint16_t));
+  };
   h->farstore.reserve(6 * (h->H.lev.size() + h->H.hl.size()));
   h->f32store.reserve(h->f32store.size() + 6 * h->H.lev.size());
   auto plan_ring = [&](const pmgl::Csr& M, const pmgl::LpLayout& lp, int nx, int ring, bool fp32) {
@@ -1167,7 +1191,11 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     pmg_hierarchy_s::COff c{};
     c.far = plan_csr(P, F);
     c.ring = ring;
-    if (fp32) { c.far32 = f32(F.v); c.push32 = f32(lp.push); c.d32 = f32(lp.dscale); }
+    if (fp32) {
+      c.far32 = f32(F.v); c.push32 = f32(lp.push); c.d32 = f32(lp.dscale);
+      c.far16 = h16(F.v, false); c.push16 = h16(lp.push, false);
+      c.farb = h16(F.v, true); c.pushb = h16(lp.push, true);
+    }
     return c;
   };
   for (const auto& L : h->H.lev) {
@@ -1307,6 +1335,16 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
                                 nullptr};
       D.Uc32 = pmgk::LpC<float>{D.N, nx, D.N / nx, cu32.ring, FU32.rp, FU32.ci, fp(cu32.far32), fp(cu32.push32),
                                 fp(cu32.d32)};
+      auto hp = [&](size_t off) { return reinterpret_cast<const __half*>(base + off); };
+      auto bp = [&](size_t off) { return reinterpret_cast<const __nv_bfloat16*>(base + off); };
+      D.Lc16 = pmgk::LpC<float, __half>{D.N, nx, D.N / nx, cl32.ring, FL32.rp, FL32.ci, hp(cl32.far16),
+                                        hp(cl32.push16), nullptr};
+      D.Uc16 = pmgk::LpC<float, __half>{D.N, nx, D.N / nx, cu32.ring, FU32.rp, FU32.ci, hp(cu32.far16),
+                                        hp(cu32.push16), fp(cu32.d32)};
+      D.Lcb = pmgk::LpC<float, __nv_bfloat16>{D.N, nx, D.N / nx, cl32.ring, FL32.rp, FL32.ci, bp(cl32.farb),
+                                              bp(cl32.pushb), nullptr};
+      D.Ucb = pmgk::LpC<float, __nv_bfloat16>{D.N, nx, D.N / nx, cu32.ring, FU32.rp, FU32.ci, bp(cu32.farb),
+                                              bp(cu32.pushb), fp(cu32.d32)};
     }
     h->dl.push_back(D);
   }
@@ -1454,7 +1492,7 @@ pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F,
   pmg_status st = check_ws(h, ws);
   if (st != PMG_OK) return st;
   if (nrhs < 1 || nrhs > ws->max_rhs || ws->R == 0 || !F || !U0 || !U || !iters || max_iter < 1 || !(tol > 0) ||
-      (precision != PMG_PREC_FP64 && precision != PMG_PREC_MIXED))
+      precision < PMG_PREC_FP64 || precision > PMG_PREC_MIXED_BF16)
     return fail(PMG_ERR_ARG, "invalid batched solve argument (workspace holds " + std::to_string(ws->R ? ws->max_rhs : 0) + " right-hand sides)");
   return solve_batched_impl(h, ws, nrhs, F, U0, tol, max_iter, precision, U, iters, hist,
                             static_cast<cudaStream_t>(stream));
@@ -1475,7 +1513,7 @@ pmg_status pmg_slots_load(pmg_handle h, pmg_ws ws, int slot0, int n, const doubl
 pmg_status pmg_slots_cycle(pmg_handle h, pmg_ws ws, int precision, double rel_tol, void* stream) {
   pmg_status st = slots_check(h, ws);
   if (st != PMG_OK) return st;
-  if (!(rel_tol > 0) || (precision != PMG_PREC_FP64 && precision != PMG_PREC_MIXED))
+  if (!(rel_tol > 0) || precision < PMG_PREC_FP64 || precision > PMG_PREC_MIXED_BF16)
     return fail(PMG_ERR_ARG, "invalid cycle argument");
   if (ws->slot_pending) return fail(PMG_ERR_BUSY, "a cycle is pending: call pmg_slots_wait first");
   if (std::find(ws->slot_state.begin(), ws->slot_state.end(), 1) == ws->slot_state.end()) return PMG_OK;

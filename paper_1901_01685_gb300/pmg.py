@@ -27,7 +27,7 @@ PMG_PROJ_INDIRECT, PMG_PROJ_DIRECT = 0, 1
 (PMG_OP_RESIDUAL, PMG_OP_SMOOTH, PMG_OP_LSOLVE, PMG_OP_USOLVE, PMG_OP_RESTRICT, PMG_OP_PROLONG_ADD,
  PMG_OP_COARSE_SOLVE, PMG_OP_VCYCLE, PMG_OP_GS_FWD, PMG_OP_GS_BWD, PMG_OP_HMG_VCYCLE) = range(11)
 PMG_MAX_LEVELS = 16
-PMG_PREC_FP64, PMG_PREC_MIXED = 0, 1
+PMG_PREC_FP64, PMG_PREC_MIXED, PMG_PREC_MIXED_FP16, PMG_PREC_MIXED_BF16 = 0, 1, 2, 3
 
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",

@@ -8,13 +8,14 @@ Sec. 5, so only rounding differs):
   iteration count:          equal within 1
   final solution:           ||u_gpu - u_oracle|| / ||u_oracle|| <= 1e-10
 
-FP32 inner cycle inside FP64 defect correction: the iteration converges to the
-same FP64 stopping criterion.  Its relative residual is recomputed by the
+FP32 inner cycle inside FP64 defect correction (factors stored in FP32, FP16
+or BF16): the iteration converges to the same FP64 stopping criterion.  Its relative residual is recomputed by the
 oracle from the returned u (it must be below 1e-8 up to rounding of the
-residual itself, 1e-8 * (1 + 1e-6)), and it needs at most two cycles more than
-the FP64 oracle: single precision only perturbs the preconditioner C by a
-relative O(1e-7), which leaves its contraction factor (~0.1 or smaller for
-these cases) practically unchanged.
+residual itself, 1e-8 * (1 + 1e-6)), and it needs only a few cycles more than
+the FP64 oracle (EXTRA_CYCLES): reduced precision perturbs only the
+preconditioner C, by a relative O(1e-7) in FP32 and O(1e-3) with 16-bit
+factors, which changes its contraction factor (~0.1 or smaller for these
+cases) only slightly.
 """
 import numpy as np
 import pytest
@@ -90,20 +91,26 @@ def test_batched_fp64_matches_oracle_per_rhs(torch_mod, pmg, oracle_mod, case):
         assert np.linalg.norm(Un[r] - uo) <= U_TOL * np.linalg.norm(uo)
 
 
+# extra cycles allowed over the FP64 oracle: FP32 perturbs the preconditioner
+# by ~1e-7 relative, FP16 / BF16 factor storage by ~5e-4 / ~4e-3 relative
+EXTRA_CYCLES = {1: 2, 2: 3, 3: 6}
+
+
 @pytest.mark.parametrize("case", CASES)
-def test_batched_mixed_precision_reaches_fp64_tolerance(torch_mod, pmg, oracle_mod, case):
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_batched_mixed_precision_reaches_fp64_tolerance(torch_mod, pmg, oracle_mod, case, prec):
     torch = torch_mod
     S, O = _pair(pmg, oracle_mod, *case)
     nrhs = 7
     F, U0 = _batch(O, nrhs, seed=9)
-    U, it, hist, st = S.solve_batched(_dev(torch, F), _dev(torch, U0), precision=pmg.PMG_PREC_MIXED)
+    U, it, hist, st = S.solve_batched(_dev(torch, F), _dev(torch, U0), precision=prec)
     assert st == 0
     Un = U.cpu().numpy()
     for r in range(nrhs):
         assert hist[it[r] - 1, r] < 1e-8
         assert _relres(O, F[r], Un[r], U0[r]) < RELRES_SLACK
         ito = O.solve(F[r], U0[r])[2]
-        assert it[r] <= ito + 2, (r, it[r], ito)
+        assert it[r] <= ito + EXTRA_CYCLES[prec], (r, it[r], ito)
 
 
 def test_rhs_result_does_not_depend_on_its_batch(torch_mod, pmg, oracle_mod):
