@@ -196,6 +196,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _direct_section(args, dist, flush, stream, world):
+    """The same workload with the paper's default projection (Sec. 3: residuals
+    restricted from p directly to p = 1, so only level p is smoothed)."""
+    import torch
+    from paper_1901_01685_gb300 import inputs, pmg
+    solvers, data = [], []
+    for p in DEGREES:
+        S = pmg.Solver(pmg.PMG_QUARTER_ANNULUS, p, LOG2H, projection=pmg.PMG_PROJ_DIRECT)
+        if not args.no_autotune:
+            S.autotune()
+        solvers.append(S)
+        data.append((torch.as_tensor(S.rhs(), device="cuda"),
+                     torch.as_tensor(inputs.initial_guess(S.N, 1), device="cuda"),
+                     torch.empty(S.N, dtype=torch.float64, device="cuda")))
+
+    def step():
+        units, iters = 0, []
+        for S, (f, u0, u) in zip(solvers, data):
+            it = S.solve(f, u0, u=u)[1]
+            units += S.N * it
+            iters.append(it)
+        return units, iters
+
+    for _ in range(args.warmup):
+        step()
+    ms, units_total, iters = [], 0, None
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        units, iters = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        units_total += units
+    t = reduce_step_time(sum(ms) / 1e3, dist, "cuda")
+    return {"workload": "as the main workload, direct projection p -> 1 (the paper's default)",
+            "value": job_value(units_total, world, t), "unit": UNIT, "iterations": iters,
+            "ms_per_step": 1e3 * t / args.steps}
+
+
 def _batched_section(args, dist, flush, stream, world):
     """Many right-hand sides on one hierarchy: plain FP64 single solves, the
     batched FP64 solve and the batched FP32-inner / FP64-defect-correction solve
@@ -205,7 +247,7 @@ def _batched_section(args, dist, flush, stream, world):
     import torch
     from paper_1901_01685_gb300 import inputs, pmg
 
-    dom, p, k = BATCHED_CASE
+    dom, p, k = (int(v) for v in args.batched_case.split(",")) if args.batched_case else BATCHED_CASE
     S = pmg.Solver(dom, p, k, max_rhs=BATCHED_NRHS)
     if not args.no_autotune:
         S.autotune()
@@ -444,8 +486,9 @@ def run_ours(args):
     t_e2e = reduce_step_time(time.perf_counter() - t0, dist, "cuda")
     e2e_value = job_value(e2e_units, world, t_e2e)
 
-    batched = None if args.no_batched or args.case else _batched_section(args, dist, flush, stream, world)
-    serving = None if args.no_serving or args.case or rank != 0 else _serving_section(args)
+    direct = None if args.no_direct or args.case else _direct_section(args, dist, flush, stream, world)
+    batched = None if args.no_batched else _batched_section(args, dist, flush, stream, world)
+    serving = None if args.no_serving or rank != 0 else _serving_section(args)
 
     if rank != 0:
         return
@@ -473,6 +516,8 @@ def run_ours(args):
                           "MDOF_iter_per_s_h2^-8": {"p2": 1.02, "p3": 0.76, "p4": 0.56, "p5": 0.41},
                           "note": "paper: benchmark-1 polynomial solution, direct projection"},
     }
+    if direct is not None:
+        line["direct_projection"] = direct
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
@@ -499,6 +544,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the many-right-hand-side section")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving section")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-projection variant of the workload")
+    ap.add_argument("--batched-case", default="", help="dom,p,log2_inv_h of the many-right-hand-side section")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()
     if args.impl == "reference":
