@@ -477,7 +477,9 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T, CT>& M, long long nnz, bool mirro
   if (inflight > 0) grid = std::min(grid, inflight * groups);
   grid = std::max(1, grid);
   unsigned* cnt = next_counter(c);
-  launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
+  // algorithmic bytes: each factor entry once (column index + value at the
+  // storage precision), row pointers, b read and x written
+  launch(c, cls, (4.0 + sizeof(CT)) * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
     cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
     pmgk::LpC<T, CT> m = M;
     int r = R;
