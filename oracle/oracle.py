@@ -287,5 +287,58 @@ class Hierarchy:
                               tol, maxit, _dp(u), _dp(hist), C.byref(it))
         return u, hist[: it.value].copy(), it.value, STATUS.get(st, st)
 
+    def bicgstab(self, f, u0, tol=1e-8, maxit=100, precond=None):
+        """BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput. 13, 1992) with
+        right preconditioning by one p-multigrid V-cycle with zero initial guess
+        per application (Sec. 5, "p-Multigrid as a preconditioner"; two
+        applications per iteration).  Stops when the recursively updated
+        residual satisfies ||r|| / ||r0|| < tol, tested after the half step (s)
+        and after the full step; an exit at the half step counts the iteration
+        in progress.  `precond(v)` replaces the V-cycle when given.
+        Returns (u, history of relative residuals per iteration, iterations,
+        status)."""
+        A = self.csr("A", 0)
+        M = precond if precond is not None else (lambda v: self.vcycle(0, v, np.zeros_like(v)))
+        x = np.array(u0, dtype=np.float64, copy=True)
+        r = np.asarray(f, dtype=np.float64) - A.matvec(x)
+        r0n = np.linalg.norm(r)
+        if r0n == 0.0:
+            return x, np.zeros(0), 0, "ok"
+        rhat = r.copy()
+        p = np.zeros_like(r)
+        v = np.zeros_like(r)
+        rho_prev = alpha = omega = 1.0
+        hist = []
+        for it in range(1, maxit + 1):
+            rho = float(rhat @ r)
+            if rho == 0.0:
+                return x, np.array(hist), it - 1, "breakdown"
+            if it == 1:
+                p = r.copy()
+            else:
+                beta = (rho / rho_prev) * (alpha / omega)
+                p = r + beta * (p - omega * v)
+            phat = M(p)
+            v = A.matvec(phat)
+            alpha = rho / float(rhat @ v)
+            s = r - alpha * v
+            if np.linalg.norm(s) / r0n < tol:
+                x = x + alpha * phat
+                hist.append(np.linalg.norm(s) / r0n)
+                return x, np.array(hist), it, "ok"
+            shat = M(s)
+            t = A.matvec(shat)
+            omega = float(t @ s) / float(t @ t)
+            x = x + alpha * phat + omega * shat
+            r = s - omega * t
+            rel = np.linalg.norm(r) / r0n
+            hist.append(rel)
+            if rel < tol:
+                return x, np.array(hist), it, "ok"
+            if not rel <= 1e10:
+                return x, np.array(hist), it, "diverged"
+            rho_prev = rho
+        return x, np.array(hist), maxit, "maxiter"
+
     def l2_error(self, u) -> float:
         return self._L.or_l2_error(self._h, _dp(np.ascontiguousarray(u, dtype=np.float64)))

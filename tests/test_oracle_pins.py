@@ -430,3 +430,60 @@ def test_spectral_radius_table2a(oracle_mod, p):
         T[:, i] = h.vcycle(0, f, e)
     rho = np.abs(np.linalg.eigvals(T)).max()
     assert rho < 0.1 and rho < 10 * max(ref[4][p - 2], 0.01), (p, rho)
+
+
+# --------------------------------------------------------------------------
+# BiCGSTAB with the p-multigrid preconditioner (Sec. 5, Table 5)
+# --------------------------------------------------------------------------
+def _spsolve(oracle_mod, h, f):
+    import scipy.sparse
+    import scipy.sparse.linalg
+    A = h.csr("A", 0)
+    return scipy.sparse.linalg.spsolve(scipy.sparse.csr_matrix((A.v, A.ci, A.rp), shape=A.shape).tocsc(), f)
+
+
+def test_bicgstab_with_exact_preconditioner_takes_one_iteration(oracle_mod):
+    """M^{-1} = A^{-1}: p-hat is the exact correction, s = 0 after the half step."""
+    from paper_1901_01685_gb300 import inputs
+    h = oracle_mod.Hierarchy(0, 3, 3)
+    f = h.rhs()
+    u, hist, it, st = h.bicgstab(f, inputs.initial_guess(h.N[0]), precond=lambda v: _spsolve(oracle_mod, h, v))
+    assert st == "ok" and it == 1
+    ue = _spsolve(oracle_mod, h, f)
+    assert np.linalg.norm(u - ue) <= 1e-12 * np.linalg.norm(ue)
+
+
+def test_bicgstab_without_preconditioner_solves_a_small_system(oracle_mod):
+    """M = I on a 64-unknown SPD system: Krylov convergence to the direct solution."""
+    from paper_1901_01685_gb300 import inputs
+    h = oracle_mod.Hierarchy(1, 2, 3)
+    f = h.rhs()
+    u, hist, it, st = h.bicgstab(f, inputs.initial_guess(h.N[0]), tol=1e-12, maxit=200, precond=lambda v: v.copy())
+    assert st == "ok" and it <= 2 * h.N[0]
+    ue = _spsolve(oracle_mod, h, f)
+    assert np.linalg.norm(u - ue) <= 1e-10 * np.linalg.norm(ue)
+    assert np.linalg.norm(h.residual(0, f, u)) <= 1e-11 * np.linalg.norm(f)
+
+
+@pytest.mark.parametrize("k", [6, 7])
+def test_table5_bicgstab_counts_annulus(oracle_mod, k):
+    """Soft pin of Table 5 (ILUT, quarter annulus): within 1 of the paper."""
+    from paper_1901_01685_gb300 import inputs
+    ref = {int(r[1]): [int(v) for v in r[2:]] for r in _golden_rows("table5_bicgstab_pmg_ilut.txt") if r[0] == "annulus"}
+    for p in (2, 3, 4):
+        h = oracle_mod.Hierarchy(0, p, k, projection=oracle_mod.DIRECT, exact=oracle_mod.U_PAPER_B1)
+        f = h.rhs()
+        u, hist, it, st = h.bicgstab(f, inputs.initial_guess(h.N[0]))
+        assert st == "ok" and abs(it - ref[k][p - 2]) <= 1, (k, p, it, hist)
+        # the recursively updated residual tracks the true one
+        true = np.linalg.norm(h.residual(0, f, u)) / np.linalg.norm(h.residual(0, f, inputs.initial_guess(h.N[0])))
+        assert true < 1e-7
+
+
+def test_table5_bicgstab_counts_cube(oracle_mod):
+    from paper_1901_01685_gb300 import inputs
+    ref = {int(r[1]): [int(v) for v in r[2:]] for r in _golden_rows("table5_bicgstab_pmg_ilut.txt") if r[0] == "cube"}
+    for p in (2, 3):
+        h = oracle_mod.Hierarchy(2, p, 3, projection=oracle_mod.DIRECT)
+        u, hist, it, st = h.bicgstab(h.rhs(), inputs.initial_guess(h.N[0]))
+        assert st == "ok" and abs(it - ref[3][p - 2]) <= 1, (p, it)
