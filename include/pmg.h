@@ -157,6 +157,19 @@ pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const d
                           double rel_tol, int max_iter, double* u_host, int* iters,
                           double* hist_host, int hist_cap, void* stream);
 
+/* BiCGSTAB (van der Vorst 1992) with the p-multigrid V-cycle as right
+ * preconditioner: each preconditioner application is one V-cycle with zero
+ * initial guess, two per iteration (Sec. 5, "p-Multigrid as a
+ * preconditioner", Table 5).  Arguments, buffers and ownership as pmg_solve;
+ * the stopping test (relative residual < rel_tol) uses the recursively updated
+ * residual after the half step and after the full step, and an exit at the
+ * half step counts the iteration in progress; res_hist_host gets one relative
+ * residual per iteration.  Errors: as pmg_solve; a breakdown (r-hat . r = 0)
+ * returns PMG_ERR_DIVERGED. */
+pmg_status pmg_solve_bicgstab(pmg_handle h, pmg_ws ws, const double* f_dev, const double* u0_dev, double rel_tol,
+                              int max_iter, double* u_dev, int* iters, double* res_hist_host, int hist_cap,
+                              void* stream);
+
 /* Precision of the batched solve's inner V-cycle: FP64; FP32 arithmetic with
  * FP32 factors; FP32 arithmetic with the ILUT factors' values stored as FP16
  * or as BF16 (widened to FP32 on load). */

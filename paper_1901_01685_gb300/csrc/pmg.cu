@@ -20,6 +20,7 @@
 #include "../../include/pmg.h"
 #include "kernels.cuh"
 #include "kernels_batched.cuh"
+#include "kernels_krylov.cuh"
 #include "setup.h"
 
 namespace {
@@ -201,6 +202,8 @@ struct pmg_workspace_s {
   CycleGraph cyc[4];
   bool graphs = true;
   long long graph_launches = 0;
+  double* kv[8] = {nullptr};          // BiCGSTAB vectors (level 0): r, r-hat, p, v, s, t, p-hat, s-hat
+  double* kd = nullptr;                // BiCGSTAB scalar results
   unsigned* flags = nullptr;
   unsigned long long* lprog = nullptr;   // per-line progress words of the line-pipelined solves
   unsigned* counters = nullptr;
@@ -236,7 +239,7 @@ namespace {
 struct WsLayout {
   size_t total = 0;
   std::vector<size_t> f, u, r, y, e, hb, hx, hr, hg;
-  size_t flags, lprog, counters, err, partial, r0, hist, f_in, u_io;
+  size_t flags, lprog, counters, err, partial, r0, hist, f_in, u_io, kv[8], kd;
   int R = 0;
   std::vector<size_t> bf, be, br, by, bt, bhb, bhx, bhr, bhg, bht;
   size_t bF = 0, bU = 0, bR = 0, br0 = 0, brel = 0, bmask = 0, bpart = 0, bstate = 0, biters = 0;
@@ -278,6 +281,8 @@ WsLayout plan_ws(const pmg_hierarchy_s* h, int max_rhs) {
     W.bstate = take(W.R * sizeof(int));
     W.biters = take(W.R * sizeof(int));
   }
+  for (auto& o : W.kv) o = take(size_t(H.lev[0].N) * sizeof(double));
+  W.kd = take(8 * sizeof(double));
   W.flags = take(size_t(maxN) * sizeof(unsigned));
   int maxLines = 1;
   for (const auto& L : H.lev) maxLines = std::max(maxLines, L.N / std::max(1, L.n1d));
@@ -684,6 +689,102 @@ pmg_status finish_launches(Ctx& c) {
     return fail(PMG_ERR_TIMEOUT, buf);
   }
   return PMG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// BiCGSTAB preconditioned by the V-cycle (Sec. 5, "p-Multigrid as a
+// preconditioner"; van der Vorst 1992): right preconditioning, one V-cycle
+// with zero initial guess per application, two applications per iteration.
+// Scalars come back to the host after each reduction.
+// ---------------------------------------------------------------------------
+pmg_status krylov_dot(Ctx& c, const double* x, const double* y, double* out) {
+  const int N = c.h->dl[0].N;
+  launch(c, PMG_K_NORM, 16.0 * N, [&] {
+    pmgk::k_dot_partial<<<pmgk::kNormBlocks, pmgk::kNormThreads, 0, c.s>>>(N, x, y, c.w->partial);
+    pmgk::k_sum_partials<<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->kd);
+  });
+  PMG_CUDA(cudaMemcpyAsync(out, c.w->kd, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  return finish_launches(c);
+}
+
+// x_hat = M^{-1} x: one V-cycle from zero (its first residual is x itself)
+void krylov_precond(Ctx& c, const double* x, double* xh) {
+  cudaMemsetAsync(xh, 0, size_t(c.h->dl[0].N) * sizeof(double), c.s);
+  vcycle(c, 0, x, xh, x);
+}
+
+pmg_status bicgstab_impl(pmg_handle h, pmg_ws ws, const double* f, const double* u0, double tol, int max_iter,
+                         double* u, int* iters, double* hist, int hist_cap, cudaStream_t s) {
+  Ctx c{h, ws, s};
+  const DevPLevel& D = h->dl[0];
+  const int N = D.N;
+  double *r = ws->kv[0], *rh = ws->kv[1], *p = ws->kv[2], *v = ws->kv[3];
+  double *sv = ws->kv[4], *t = ws->kv[5], *ph = ws->kv[6], *sh = ws->kv[7];
+  const int gb = grid_for(N, 256, h->sms * 8);
+  auto sub_scaled = [&](const double* x, double a, const double* y, double* out) {
+    launch(c, PMG_K_NORM, 24.0 * N, [&] { pmgk::k_sub_scaled<<<gb, 256, 0, c.s>>>(N, x, a, y, out); });
+  };
+  auto matvec = [&](const double* x, double* y) {
+    launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 16.0 * D.N,
+           [&] { spmv<1>(D.A, D.avg_nnz, x, nullptr, y, c.s, h->sms); });
+  };
+  if (iters) *iters = 0;
+  pmg_status st = begin_launches(c);
+  if (st != PMG_OK) return st;
+  if (u != u0) PMG_CUDA(cudaMemcpyAsync(u, u0, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  residual(c, 0, f, u, r);
+  double rr = 0.0;
+  if ((st = krylov_dot(c, r, r, &rr)) != PMG_OK) return st;
+  const double r0n = std::sqrt(rr);
+  if (r0n == 0.0) return PMG_OK;
+  PMG_CUDA(cudaMemcpyAsync(rh, r, size_t(N) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PMG_CUDA(cudaMemsetAsync(p, 0, size_t(N) * sizeof(double), s));
+  PMG_CUDA(cudaMemsetAsync(v, 0, size_t(N) * sizeof(double), s));
+  double rho_prev = 1.0, alpha = 1.0, omega = 1.0;
+  for (int it = 1; it <= max_iter; ++it) {
+    if ((st = begin_launches(c)) != PMG_OK) return st;
+    double rho = 0.0;
+    if ((st = krylov_dot(c, rh, r, &rho)) != PMG_OK) return st;
+    if (rho == 0.0) return fail(PMG_ERR_DIVERGED, "BiCGSTAB breakdown (r-hat . r = 0)");
+    const double beta = it == 1 ? 0.0 : (rho / rho_prev) * (alpha / omega);
+    launch(c, PMG_K_NORM, 32.0 * N, [&] { pmgk::k_bicg_direction<<<gb, 256, 0, c.s>>>(N, beta, omega, r, v, p); });
+    krylov_precond(c, p, ph);
+    matvec(ph, v);
+    double rhv = 0.0;
+    if ((st = krylov_dot(c, rh, v, &rhv)) != PMG_OK) return st;
+    alpha = rho / rhv;
+    sub_scaled(r, alpha, v, sv);
+    double ss = 0.0;
+    if ((st = krylov_dot(c, sv, sv, &ss)) != PMG_OK) return st;
+    const double srel = std::sqrt(ss) / r0n;
+    if (srel < tol) {
+      launch(c, PMG_K_NORM, 24.0 * N,
+             [&] { pmgk::k_bicg_solution<<<gb, 256, 0, c.s>>>(N, alpha, ph, 0.0, nullptr, u); });
+      if (hist && it - 1 < hist_cap) hist[it - 1] = srel;
+      if (iters) *iters = it;
+      PMG_CUDA(cudaStreamSynchronize(s));
+      return PMG_OK;
+    }
+    if ((st = begin_launches(c)) != PMG_OK) return st;
+    krylov_precond(c, sv, sh);
+    matvec(sh, t);
+    double ts = 0.0, tt = 0.0;
+    if ((st = krylov_dot(c, t, sv, &ts)) != PMG_OK) return st;
+    if ((st = krylov_dot(c, t, t, &tt)) != PMG_OK) return st;
+    omega = ts / tt;
+    launch(c, PMG_K_NORM, 32.0 * N,
+           [&] { pmgk::k_bicg_solution<<<gb, 256, 0, c.s>>>(N, alpha, ph, omega, sh, u); });
+    sub_scaled(sv, omega, t, r);
+    double r2 = 0.0;
+    if ((st = krylov_dot(c, r, r, &r2)) != PMG_OK) return st;
+    const double rel = std::sqrt(r2) / r0n;
+    if (hist && it - 1 < hist_cap) hist[it - 1] = rel;
+    if (iters) *iters = it;
+    if (rel < tol) return PMG_OK;
+    if (!(rel <= 1e10)) return fail(PMG_ERR_DIVERGED, "relative residual exceeded 1e10");
+    rho_prev = rho;
+  }
+  return fail(PMG_ERR_MAXITER, "maximum number of BiCGSTAB iterations reached");
 }
 
 pmg_status solve_impl(pmg_handle h, pmg_ws ws, const double* f, const double* u0, double tol, int max_iter,
@@ -1446,6 +1547,8 @@ pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t byt
     std::memset(w->hm_block, 0, hb);
     w->slot_state.assign(size_t(W.R), 0);
   }
+  for (int k = 0; k < 8; ++k) w->kv[k] = P(W.kv[k]);
+  w->kd = P(W.kd);
   w->flags = reinterpret_cast<unsigned*>(base + W.flags);
   w->lprog = reinterpret_cast<unsigned long long*>(base + W.lprog);
   w->counters = reinterpret_cast<unsigned*>(base + W.counters);
@@ -1469,6 +1572,14 @@ pmg_status pmg_solve(pmg_handle h, pmg_ws ws, const double* f, const double* u0,
   if (st != PMG_OK) return st;
   if (!f || !u0 || !u || max_iter < 1 || !(tol > 0)) return fail(PMG_ERR_ARG, "invalid solve argument");
   return solve_impl(h, ws, f, u0, tol, max_iter, u, iters, hist, hist_cap, static_cast<cudaStream_t>(stream));
+}
+
+pmg_status pmg_solve_bicgstab(pmg_handle h, pmg_ws ws, const double* f, const double* u0, double tol,
+                              int max_iter, double* u, int* iters, double* hist, int hist_cap, void* stream) {
+  pmg_status st = check_ws(h, ws);
+  if (st != PMG_OK) return st;
+  if (!f || !u0 || !u || max_iter < 1 || !(tol > 0)) return fail(PMG_ERR_ARG, "invalid solve argument");
+  return bicgstab_impl(h, ws, f, u0, tol, max_iter, u, iters, hist, hist_cap, static_cast<cudaStream_t>(stream));
 }
 
 pmg_status pmg_solve_host(pmg_handle h, pmg_ws ws, const double* f_host, const double* u0_host, double tol,

@@ -31,7 +31,7 @@ PMG_PREC_FP64, PMG_PREC_MIXED, PMG_PREC_MIXED_FP16, PMG_PREC_MIXED_BF16 = 0, 1, 
 
 # every symbol include/pmg.h declares
 EXPORTS = ("pmg_default_options", "pmg_setup", "pmg_info", "pmg_upload", "pmg_rhs", "pmg_workspace_bytes",
-           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_batched", "pmg_slots_load", "pmg_slots_cycle",
+           "pmg_workspace_create", "pmg_solve", "pmg_solve_host", "pmg_solve_bicgstab", "pmg_solve_batched", "pmg_slots_load", "pmg_slots_cycle",
            "pmg_slots_wait", "pmg_slots_read", "pmg_slots_release", "pmg_autotune", "pmg_set_kernels", "pmg_apply",
            "pmg_export_csr",
            "pmg_export_lumped", "pmg_l2_error", "pmg_ws_profile", "pmg_ws_stats", "pmg_lsolve_noalloc",
@@ -109,6 +109,7 @@ def lib():
         L.pmg_workspace_bytes.argtypes = [vp, C.c_int, C.POINTER(C.c_size_t)]
         L.pmg_workspace_create.argtypes = [vp, C.c_int, vp, C.c_size_t, vp, C.POINTER(vp)]
         L.pmg_solve.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
+        L.pmg_solve_bicgstab.argtypes = [vp, vp, vp, vp, C.c_double, C.c_int, vp, ip, dp, C.c_int, vp]
         L.pmg_solve_host.argtypes = [vp, vp, dp, dp, C.c_double, C.c_int, dp, ip, dp, C.c_int, vp]
         L.pmg_solve_batched.argtypes = [vp, vp, C.c_int, vp, vp, C.c_double, C.c_int, C.c_int, vp, ip, dp, vp]
         L.pmg_slots_load.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp, vp]
@@ -223,6 +224,15 @@ def pmg_solve(h, ws, f, u0, rel_tol, max_iter, u, hist_cap=256, stream=None, all
     st = lib().pmg_solve(h, ws, _ptr(f), _ptr(u0), rel_tol, max_iter, _ptr(u), C.byref(iters), _dp(hist),
                          hist_cap, _stream(stream))
     _check(st, "pmg_solve", allow)
+    return iters.value, hist[: min(iters.value, hist_cap)].copy(), st
+
+
+def pmg_solve_bicgstab(h, ws, f, u0, rel_tol, max_iter, u, hist_cap=256, stream=None, allow=()):
+    iters = C.c_int()
+    hist = np.zeros(hist_cap)
+    st = lib().pmg_solve_bicgstab(h, ws, _ptr(f), _ptr(u0), rel_tol, max_iter, _ptr(u), C.byref(iters), _dp(hist),
+                                  hist_cap, _stream(stream))
+    _check(st, "pmg_solve_bicgstab", allow)
     return iters.value, hist[: min(iters.value, hist_cap)].copy(), st
 
 
@@ -386,6 +396,14 @@ class Solver:
         if u is None:
             u = torch.empty_like(u0)
         it, hist, st = pmg_solve(self.h, self.ws, f, u0, rel_tol, max_iter, u, allow=allow)
+        return u, it, hist, st
+
+    def solve_bicgstab(self, f, u0, rel_tol=1e-8, max_iter=100, u=None, allow=()):
+        """BiCGSTAB preconditioned by one V-cycle per application (Sec. 5, Table 5)."""
+        import torch
+        if u is None:
+            u = torch.empty_like(u0)
+        it, hist, st = pmg_solve_bicgstab(self.h, self.ws, f, u0, rel_tol, max_iter, u, allow=allow)
         return u, it, hist, st
 
     def autotune(self):

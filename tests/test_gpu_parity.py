@@ -193,3 +193,31 @@ def test_repeated_solves_are_deterministic(torch_mod, pmg, oracle_mod):
     a, ita, ha, _ = S.solve(f, u0)
     b, itb, hb, _ = S.solve(f, u0)
     assert ita == itb and np.array_equal(ha, hb) and torch.equal(a, b)
+
+
+def _check_bicgstab(torch, S, O, seed=1):
+    f = O.rhs()
+    u0 = inputs.initial_guess(O.N[0], seed)
+    u, it, hist, st = S.solve_bicgstab(_dev(torch, f), _dev(torch, u0))
+    uo, ho, ito, sto = O.bicgstab(f, u0)
+    assert st == 0 and sto == "ok"
+    assert abs(it - ito) <= 1, (it, ito)
+    m = min(it, ito)
+    assert np.abs(hist[:m] - ho[:m]).max() <= HIST_TOL, (hist, ho)
+    if it == ito:
+        assert np.linalg.norm(u.cpu().numpy() - uo) <= U_TOL * np.linalg.norm(uo)
+    return it, hist
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_bicgstab_matches_oracle(torch_mod, pmg, oracle_mod, case):
+    """BiCGSTAB preconditioned by the V-cycle (Sec. 5, Table 5) against the oracle's."""
+    S, O = _pair(pmg, oracle_mod, *case)
+    _check_bicgstab(torch_mod, S, O)
+
+
+def test_bicgstab_full_size_annulus(torch_mod, pmg, oracle_mod):
+    S = pmg.Solver(0, 3, 8)
+    O = oracle_mod.Hierarchy(0, 3, 8)
+    it, hist = _check_bicgstab(torch_mod, S, O)
+    assert hist[-1] < 1e-8 and it <= 3
