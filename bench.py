@@ -465,6 +465,31 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     total_ms = sum(c["ms"] for c in classes.values())
 
+    # the same solves with BiCGSTAB preconditioned by the V-cycle (Sec. 5, Table 5)
+    bicg = None
+    if not args.no_bicgstab:
+        def bstep():
+            its = []
+            for S, f, u0, u in zip(solvers, fdev, u0dev, udev):
+                its.append(S.solve_bicgstab(f, u0, u=u)[1])
+            return its
+        for _ in range(args.warmup):
+            bstep()
+        bms, bits = [], None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bits = bstep()
+            e1.record(stream)
+            e1.synchronize()
+            bms.append(e0.elapsed_time(e1))
+        tb = reduce_step_time(sum(bms) / 1e3, dist, "cuda")
+        bicg = {"ms_per_step": 1e3 * tb / args.steps, "iterations": bits, "vcycles": [2 * i for i in bits],
+                "speedup_vs_stationary": t_dev / tb,
+                "note": "one iteration = two V-cycles (preconditioner applications) + two SpMVs"}
+
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     host = []
     for S, f, u0 in zip(solvers, fdev, u0dev):
@@ -518,6 +543,8 @@ def run_ours(args):
     }
     if direct is not None:
         line["direct_projection"] = direct
+    if bicg is not None:
+        line["bicgstab"] = bicg
     if batched is not None:
         line["batched"] = batched
     if serving is not None:
@@ -545,6 +572,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default kernel variants")
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving section")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-projection variant of the workload")
+    ap.add_argument("--no-bicgstab", action="store_true", help="skip the BiCGSTAB timing of the workload")
     ap.add_argument("--batched-case", default="", help="dom,p,log2_inv_h of the many-right-hand-side section")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()
