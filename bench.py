@@ -335,29 +335,26 @@ def _serving_section(args):
                        "sides each, 1e-8 relres; saturation run (all requests at t=0, plain FP64), then Poisson "
                        "arrivals at 0.8x the saturation request rate, plain FP64 and FP32-inner, same arrivals",
            "slots_per_key": SERVING_SLOTS}
-    servers = {}
-    for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED)):
-        be = serve.GpuBackend(autotune=not args.no_autotune)
-        srv = serve.Server(be, slots=SERVING_SLOTS, precision=prec)
-        t0 = time.perf_counter()
-        srv.prewarm(keys)
-        servers[name] = (srv, time.perf_counter() - t0)
-    srv0 = servers["fp64"][0]
-    rhs = {k: (srv0.keys[k].handle["S"].rhs(), srv0.keys[k].handle["S"].N) for k in keys}
+    be = serve.GpuBackend(autotune=not args.no_autotune)
+    srv = serve.Server(be, slots=SERVING_SLOTS, precision=pmg.PMG_PREC_FP64)
+    t0 = time.perf_counter()
+    srv.prewarm(keys)
+    out["setup_s"] = time.perf_counter() - t0
+    rhs = {k: (srv.keys[k].handle["S"].rhs(), srv.keys[k].handle["S"].N) for k in keys}
 
     def fresh():
         return serve.request_mix(keys, SERVING_REQUESTS, lambda k: rhs[k], seed=11, max_rhs=16)
 
-    sat = serve.run_stream(srv0, fresh(), np.zeros(SERVING_REQUESTS))
+    sat = serve.run_stream(srv, fresh(), np.zeros(SERVING_REQUESTS))
     rate = 0.8 * SERVING_REQUESTS / sat["makespan_s"]
     out["saturation_fp64"] = sat
     out["arrival_rate_per_s"] = rate
     arrivals = serve.poisson_arrivals(SERVING_REQUESTS, rate, seed=7)
-    for name, (srv, t_setup) in servers.items():
-        stats = serve.run_stream(srv, fresh(), arrivals)
-        stats["setup_s"] = t_setup
-        out[name] = stats
-        srv.close()
+    for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED)):
+        srv.precision = prec
+        srv.cycles = 0
+        out[name] = serve.run_stream(srv, fresh(), arrivals)
+    srv.close()
     out["mixed_vs_fp64_solves_per_s"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
     return out
 
