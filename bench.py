@@ -279,6 +279,35 @@ def _batched_section(args, dist, flush, stream, world):
 
     u1 = torch.empty(N, dtype=torch.float64, device="cuda")
     t_single, single = timed(lambda: S.solve(F[0], U0[0], u=u1)[1])
+
+    # The bandwidth kernels at a size larger than L2 (this hierarchy's level 0:
+    # A has ~21 M non-zeros, 257 MB): residual SpMV, restriction, prolongation,
+    # each launch preceded by an L2 flush, timed by the library's per-launch
+    # events; GB/s of algorithmic bytes against the measured HBM copy rate.
+    Nc = S.info["n"][1]
+    xc = torch.ones(Nc, dtype=torch.float64, device="cuda")
+    yc = torch.empty(Nc, dtype=torch.float64, device="cuda")
+    y = torch.empty(N, dtype=torch.float64, device="cuda")
+    pmg.pmg_ws_profile(S.ws, True)
+    pmg.pmg_ws_stats(S.ws, reset=True)
+    for _ in range(max(args.steps, 10)):
+        flush.fill_(1.0)
+        S.apply(pmg.PMG_OP_RESIDUAL, 0, U0[0], F[0], y)
+        flush.fill_(1.0)
+        S.apply(pmg.PMG_OP_RESTRICT, 0, U0[0], None, yc)
+        flush.fill_(1.0)
+        S.apply(pmg.PMG_OP_PROLONG_ADD, 0, xc, F[0], y)
+    pc = pmg.pmg_ws_stats(S.ws, reset=True).as_dict()["per_class"]
+    pmg.pmg_ws_profile(S.ws, False)
+    peak, peak_kind = _peaks()
+    bw = {}
+    for cls in ("residual", "transfer"):
+        c = pc[cls]
+        gbs = c["bytes"] / (c["ms"] / 1e3) / 1e9 if c["ms"] else None
+        bw[cls] = {"launches": c["launches"], "avg_ms": c["ms"] / max(c["launches"], 1), "GBps": gbs,
+                   "frac_of_hbm": gbs / peak if gbs else None}
+    bw["peak_GBps"] = peak
+    bw["peak_kind"] = peak_kind
     res = {}
     for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED),
                        ("mixed_fp16_factors", pmg.PMG_PREC_MIXED_FP16), ("mixed_bf16_factors", pmg.PMG_PREC_MIXED_BF16)):
@@ -317,7 +346,8 @@ def _batched_section(args, dist, flush, stream, world):
             **res,
             "mixed_vs_plain_fp64_solves_per_s": res["mixed"]["solves_per_s"] * t_single / world,
             "mixed_vs_batched_fp64_solves_per_s": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"],
-            "error_vs_fp64": errors}
+            "error_vs_fp64": errors,
+            "bandwidth_kernels_cold_l2": bw}
 
 
 def _serving_section(args):
