@@ -82,27 +82,10 @@ __global__ void __launch_bounds__(256) k_spmv(Csr A, const double* __restrict__ 
   const int group = (blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int ngroups = (gridDim.x * blockDim.x) / W;
   for (int row = group; row < A.nr; row += ngroups) {
-    const int beg = __ldg(A.rp + row), end = __ldg(A.rp + row + 1);
-    double s0 = 0.0, s1 = 0.0;
-    // up to four entries per lane in flight: every column index and value of
-    // the round is requested before the gathers that depend on them
-    for (int t = beg + lane; t < end; t += 4 * W) {
-      int c[4];
-      double v[4], xv[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool in = t + k * W < end;
-        c[k] = in ? __ldg(A.ci + t + k * W) : -1;
-        v[k] = in ? __ldg(A.v + t + k * W) : 0.0;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) xv[k] = c[k] >= 0 ? __ldg(x + c[k]) : 0.0;
-      s0 = fma(v[0], xv[0], s0);
-      s1 = fma(v[1], xv[1], s1);
-      s0 = fma(v[2], xv[2], s0);
-      s1 = fma(v[3], xv[3], s1);
-    }
-    double s = group_sum<W>(s0 + s1);
+    const int beg = A.rp[row], end = A.rp[row + 1];
+    double s = 0.0;
+    for (int t = beg + lane; t < end; t += W) s += A.v[t] * x[A.ci[t]];
+    s = group_sum<W>(s);
     if (lane == 0) {
       if (MODE == 0) y[row] = b[row] - s;
       else if (MODE == 1) y[row] = s;

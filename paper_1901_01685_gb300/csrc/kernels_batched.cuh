@@ -104,25 +104,14 @@ __global__ void __launch_bounds__(256) k_spmm(TCsr<TA> A, int R, const TX* __res
     const int row = (int)(w / G), g = (int)(w % G);
     const int col = g * 32 + lane;
     using Acc = typename AccT<TA, TX>::type;
-    const int beg = __ldg(A.rp + row), end = __ldg(A.rp + row + 1);
+    const int beg = A.rp[row], end = A.rp[row + 1];
     Acc a0 = 0, a1 = 0;
-    // four entries in flight: indices and values first, then the gathers
-    for (int t = beg; t < end; t += 4) {
-      int c[4];
-      Acc v[4], xv[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const bool in = t + k < end;
-        c[k] = in ? __ldg(A.ci + t + k) : -1;
-        v[k] = in ? (Acc)__ldg(A.v + t + k) : Acc(0);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) xv[k] = c[k] >= 0 ? (Acc)__ldg(X + (size_t)c[k] * R + col) : Acc(0);
-      a0 = fma(v[0], xv[0], a0);
-      a1 = fma(v[1], xv[1], a1);
-      a0 = fma(v[2], xv[2], a0);
-      a1 = fma(v[3], xv[3], a1);
+    int t = beg;
+    for (; t + 1 < end; t += 2) {
+      a0 = fma((Acc)A.v[t], (Acc)X[(size_t)A.ci[t] * R + col], a0);
+      a1 = fma((Acc)A.v[t + 1], (Acc)X[(size_t)A.ci[t + 1] * R + col], a1);
     }
+    if (t < end) a0 = fma((Acc)A.v[t], (Acc)X[(size_t)A.ci[t] * R + col], a0);
     const Acc s = a0 + a1;
     const size_t o = (size_t)row * R + col;
     if (MODE == 0) Y[o] = (TY)((Acc)B[o] - s);
