@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "pmg_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liboracle.so")
 
-ANNULUS, SQUARE, CUBE = 0, 1, 2
+ANNULUS, SQUARE, CUBE, CDR_SQUARE = 0, 1, 2, 3
 U_SINPROD, U_PAPER_B1 = 0, 1
 INDIRECT, DIRECT = 0, 1
 STATUS = {0: "ok", 1: "arg", 2: "oom", 3: "zero_pivot", 4: "diverged", 5: "maxiter"}

@@ -58,7 +58,13 @@
 
 #define OR_PI 3.14159265358979323846
 
-enum { OR_ANNULUS = 0, OR_SQUARE = 1, OR_CUBE = 2 };
+enum { OR_ANNULUS = 0, OR_SQUARE = 1, OR_CUBE = 2, OR_CDR_SQUARE = 3 };
+
+/* Benchmark 2 (Sec. 2): -div(D grad u) + v . grad u + R u = f on the unit
+ * square with these coefficients; the other benchmarks have D = I, v = 0, R = 0. */
+static const double CDR_D[2][2] = {{1.2, -0.7}, {-0.4, 0.9}};
+static const double CDR_V[2] = {0.4, -0.2};
+static const double CDR_R = 0.3;
 enum { OR_U_SINPROD = 0, OR_U_PAPER_B1 = 1 };
 enum { OR_INDIRECT = 0, OR_DIRECT = 1 };
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_OOM = 2, OR_ERR_ZERO_PIVOT = 3,
@@ -173,6 +179,14 @@ static double f_source(int dom, int ex, int d, const double* X) {
   if (ex == OR_U_PAPER_B1 && dom == OR_ANNULUS) {
     double x = X[0], y = X[1];
     return 2.0 * x * (x * x * x * x + 22.0 * x * x * y * y - 5.0 * x * x + 21.0 * y * y * y * y - 45.0 * y * y + 4.0);
+  }
+  if (dom == OR_CDR_SQUARE) {
+    /* f = -sum_ab D_ab d_a d_b u + v . grad u + R u for u = sin(pi x) sin(pi y) */
+    double sx = sin(OR_PI * X[0]), sy = sin(OR_PI * X[1]), cx = cos(OR_PI * X[0]), cy = cos(OR_PI * X[1]);
+    double uxx = -OR_PI * OR_PI * sx * sy, uyy = uxx, uxy = OR_PI * OR_PI * cx * cy;
+    double ux = OR_PI * cx * sy, uy = OR_PI * sx * cy;
+    return -(CDR_D[0][0] * uxx + CDR_D[0][1] * uxy + CDR_D[1][0] * uxy + CDR_D[1][1] * uyy) +
+           CDR_V[0] * ux + CDR_V[1] * uy + CDR_R * sx * sy;
   }
   double u = 1.0;
   for (int a = 0; a < d; ++a) u *= sin(OR_PI * X[a]);
@@ -342,7 +356,14 @@ static int assemble(int dom, int d, int ne, int q, int r, int kind, int with_loa
           /* slot of the offset (trial index - test index + q) per direction */
           long long slot = slot_j[lj] - slot_i[li] + slot_q;
           double integrand;
-          if (kind == K_STIFF) {
+          if (kind == K_STIFF && dom == OR_CDR_SQUARE) {
+            /* (D grad phi_j) . grad phi_i + (v . grad phi_j) phi_i + R phi_j phi_i, i test, j trial */
+            integrand = CDR_R * phq[li] * phr[lj];
+            for (int a = 0; a < 2; ++a) {
+              integrand += CDR_V[a] * ghr[lj * 3 + a] * phq[li];
+              for (int b = 0; b < 2; ++b) integrand += CDR_D[a][b] * ghr[lj * 3 + b] * ghq[li * 3 + a];
+            }
+          } else if (kind == K_STIFF) {
             integrand = 0.0;
             for (int c = 0; c < d; ++c) integrand += ghq[li * 3 + c] * ghr[lj * 3 + c];
           } else {
@@ -785,7 +806,7 @@ static int build_operator(or_hier* h, int ne, int q, csr* A, double** ML, double
 or_hier* or_setup(int dom, int p, int k, double tau, double fill, int proj, int ex,
                   int nu1, int nu2, int ccyc, int* status) {
   *status = OR_ERR_ARG;
-  if (dom < 0 || dom > 2 || p < 2 || p > 8 || k < 3 || k > 12 || ccyc < 1 || nu1 < 0 || nu2 < 0) return NULL;
+  if (dom < 0 || dom > 3 || p < 2 || p > 8 || k < 3 || k > 12 || ccyc < 1 || nu1 < 0 || nu2 < 0) return NULL;
   if (dom == OR_CUBE && k > 6) return NULL;
   or_hier* h = calloc(1, sizeof(or_hier));
   if (!h) { *status = OR_ERR_OOM; return NULL; }

@@ -487,3 +487,62 @@ def test_table5_bicgstab_counts_cube(oracle_mod):
         h = oracle_mod.Hierarchy(2, p, 3, projection=oracle_mod.DIRECT)
         u, hist, it, st = h.bicgstab(h.rhs(), inputs.initial_guess(h.N[0]))
         assert st == "ok" and abs(it - ref[3][p - 2]) <= 1, (p, it)
+
+
+# --------------------------------------------------------------------------
+# Benchmark 2: convection-diffusion-reaction on the unit square (Sec. 2)
+# --------------------------------------------------------------------------
+CDR_D = ((1.2, -0.7), (-0.4, 0.9))
+CDR_V = (0.4, -0.2)
+CDR_R = 0.3
+
+
+def test_cdr_source_is_the_pde_applied_to_u(oracle_mod):
+    import sympy as sp
+    x, y = sp.symbols("x y")
+    u = sp.sin(sp.pi * x) * sp.sin(sp.pi * y)
+    X = (x, y)
+    f = -sum(CDR_D[a][b] * sp.diff(u, X[a], X[b]) for a in range(2) for b in range(2))
+    f += sum(CDR_V[b] * sp.diff(u, X[b]) for b in range(2)) + CDR_R * u
+    ff = sp.lambdify((x, y), f, "math")
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        P = rng.uniform(0.0, 1.0, 2)
+        assert abs(oracle_mod.f_source(oracle_mod.CDR_SQUARE, 0, P[0], P[1], 0.0) - ff(*P)) < 1e-11 * (1 + abs(ff(*P)))
+
+
+@pytest.mark.parametrize("k,q", [(3, 2), (3, 3), (4, 2)])
+def test_cdr_row_sums_are_reaction_times_basis_integrals(oracle_mod, k, q):
+    """Partition of unity: sum_j grad Phi_j = 0, so before boundary conditions the
+    diffusion and convection terms vanish from every row sum, leaving
+    R int Phi_i = R (lumped mass)_ii."""
+    A = _sparse(oracle_mod.full_matrix(oracle_mod.CDR_SQUARE, k, q, q, "stiff"))
+    M = _sparse(oracle_mod.full_matrix(oracle_mod.CDR_SQUARE, k, q, q, "mass"))
+    rs = np.asarray(A.sum(axis=1)).ravel()
+    ml = np.asarray(M.sum(axis=1)).ravel()
+    assert np.abs(rs - CDR_R * ml).max() < 1e-13 * abs(A).max()
+    # the operator is not symmetric: convection and the skew part of D
+    assert abs(A - A.T).max() > 1e-3 * abs(A).max()
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_cdr_l2_convergence_rate(oracle_mod, p):
+    errs = [_direct_error(oracle_mod, oracle_mod.CDR_SQUARE, p, k, 0) for k in (3, 4, 5)]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) > p + 1 - 0.2, (errs, rates)
+
+
+def test_cdr_table4_and_table5_counts(oracle_mod):
+    """Soft pins (within 2 for V-cycles, 1 for BiCGSTAB iterations) of the
+    benchmark-2 rows of Tables 4 and 5 at h = 2^-6."""
+    from paper_1901_01685_gb300 import inputs
+    rows = _golden_rows("table4_table5_cdr.txt")
+    vc = {int(r[1]): [int(v) for v in r[2:]] for r in rows if r[0] == "vcycles"}
+    bi = {int(r[1]): [int(v) for v in r[2:]] for r in rows if r[0] == "bicgstab"}
+    for p in (2, 3, 4):
+        h = oracle_mod.Hierarchy(oracle_mod.CDR_SQUARE, p, 6, projection=oracle_mod.DIRECT)
+        f, u0 = h.rhs(), inputs.initial_guess(h.N[0])
+        _, hist, it, st = h.solve(f, u0)
+        assert st == "ok" and abs(it - vc[6][p - 2]) <= 2, (p, it, hist)
+        _, hist, it, st = h.bicgstab(f, u0)
+        assert st == "ok" and abs(it - bi[6][p - 2]) <= 1, (p, it, hist)
