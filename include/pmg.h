@@ -49,7 +49,11 @@ typedef enum {
   PMG_ERR_STATE = 9       /* call out of order (e.g. solve before upload) */
 } pmg_status;
 
-typedef enum { PMG_QUARTER_ANNULUS = 0, PMG_UNIT_SQUARE = 1, PMG_UNIT_CUBE = 2 } pmg_domain;
+/* Benchmarks of Sec. 2: 1 quarter annulus (Poisson), unit square (Poisson),
+ * 4 unit cube (Poisson), 2 unit square with the convection-diffusion-reaction
+ * coefficients D = [[1.2, -0.7], [-0.4, 0.9]], v = (0.4, -0.2), R = 0.3
+ * (non-symmetric operator; the P1 levels rediscretise the same equation). */
+typedef enum { PMG_QUARTER_ANNULUS = 0, PMG_UNIT_SQUARE = 1, PMG_UNIT_CUBE = 2, PMG_CDR_SQUARE = 3 } pmg_domain;
 
 /* Manufactured solution used for the load vector and the Dirichlet data.
  * PMG_U_SINPROD: u = sin(pi x) sin(pi y) [sin(pi z)];

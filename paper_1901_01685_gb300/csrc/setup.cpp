@@ -158,11 +158,24 @@ double exact_u(int dom, int ex, int d, const double* X) {
   return v;
 }
 
-// -Lap(u) of the manufactured solutions.
+// Benchmark 2 (Sec. 2): -div(D grad u) + v . grad u + R u on the unit square.
+constexpr double kCdrD[2][2] = {{1.2, -0.7}, {-0.4, 0.9}};
+constexpr double kCdrV[2] = {0.4, -0.2};
+constexpr double kCdrR = 0.3;
+
+// The PDE applied to the manufactured solutions (-Lap(u) for benchmarks 1 and 4).
 double source_f(int dom, int ex, int d, const double* X) {
   if (dom == PMG_QUARTER_ANNULUS && ex == PMG_U_PAPER_B1) {
     const double x = X[0], y = X[1], x2 = x * x, y2 = y * y;
     return 2.0 * x * (x2 * x2 + 22.0 * x2 * y2 - 5.0 * x2 + 21.0 * y2 * y2 - 45.0 * y2 + 4.0);
+  }
+  if (dom == PMG_CDR_SQUARE) {
+    // u = sin(pi x) sin(pi y): u_xx = u_yy = -pi^2 u, u_xy = pi^2 cos cos
+    const double sx = std::sin(kPi * X[0]), sy = std::sin(kPi * X[1]);
+    const double cx = std::cos(kPi * X[0]), cy = std::cos(kPi * X[1]);
+    const double u = sx * sy, pi2 = kPi * kPi;
+    return pi2 * (kCdrD[0][0] + kCdrD[1][1]) * u - pi2 * (kCdrD[0][1] + kCdrD[1][0]) * cx * cy +
+           kPi * (kCdrV[0] * cx * sy + kCdrV[1] * sx * cy) + kCdrR * u;
   }
   double v = double(d) * kPi * kPi;
   for (int a = 0; a < d; ++a) v *= std::sin(kPi * X[a]);
@@ -281,7 +294,17 @@ void assemble(int dom, int d, int ne, int q, int r, Form form, bool want_load, i
                     }
                 }
               }
-              if (form == kStiffness) {
+              if (form == kStiffness && dom == PMG_CDR_SQUARE) {
+                // test a, trial b: (D grad phi_b) . grad phi_a + (v . grad phi_b) phi_a + R phi_b phi_a
+                for (int a = 0; a < nlq; ++a) {
+                  const double ga0 = dw * gq[a * 3 + 0], ga1 = dw * gq[a * 3 + 1], pa = dw * phq[a];
+                  const double w0 = ga0 * kCdrD[0][0] + ga1 * kCdrD[1][0] + pa * kCdrV[0];
+                  const double w1 = ga0 * kCdrD[0][1] + ga1 * kCdrD[1][1] + pa * kCdrV[1];
+                  const double wr = pa * kCdrR;
+                  double* row = &Ke[size_t(a) * nlr];
+                  for (int b = 0; b < nlr; ++b) row[b] += w0 * gr[b * 3 + 0] + w1 * gr[b * 3 + 1] + wr * phr[b];
+                }
+              } else if (form == kStiffness) {
                 for (int a = 0; a < nlq; ++a) {
                   const double g0 = dw * gq[a * 3 + 0], g1 = dw * gq[a * 3 + 1], g2 = dw * gq[a * 3 + 2];
                   double* row = &Ke[size_t(a) * nlr];
@@ -827,7 +850,7 @@ int critical_path(const Csr& T, bool lower) {
 }
 
 pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierarchy& H, std::string& err) {
-  if (dom < 0 || dom > 2) { err = "unknown domain"; return PMG_ERR_ARG; }
+  if (dom < 0 || dom > 3) { err = "unknown domain"; return PMG_ERR_ARG; }
   if (p < 2 || p > 8) { err = "p must be in [2, 8]"; return PMG_ERR_ARG; }
   if (k < 3 || k > 12 || (dom == PMG_UNIT_CUBE && k > 6)) { err = "log2_inv_h out of range"; return PMG_ERR_ARG; }
   if (opt.coarse_cycles < 1 || opt.nu_pre < 0 || opt.nu_post < 0 || opt.drop_tol < 0 || opt.fill_factor <= 0 ||

@@ -21,7 +21,7 @@ PMG_OK, PMG_ERR_ARG, PMG_ERR_OOM, PMG_ERR_ZERO_PIVOT, PMG_ERR_DIVERGED, PMG_ERR_
     PMG_ERR_TIMEOUT, PMG_ERR_CUDA, PMG_ERR_BUSY, PMG_ERR_STATE = range(10)
 STATUS_NAMES = {0: "ok", 1: "arg", 2: "oom", 3: "zero_pivot", 4: "diverged", 5: "maxiter",
                 6: "timeout", 7: "cuda", 8: "busy", 9: "state"}
-PMG_QUARTER_ANNULUS, PMG_UNIT_SQUARE, PMG_UNIT_CUBE = 0, 1, 2
+PMG_QUARTER_ANNULUS, PMG_UNIT_SQUARE, PMG_UNIT_CUBE, PMG_CDR_SQUARE = 0, 1, 2, 3
 PMG_U_SINPROD, PMG_U_PAPER_B1 = 0, 1
 PMG_PROJ_INDIRECT, PMG_PROJ_DIRECT = 0, 1
 (PMG_OP_RESIDUAL, PMG_OP_SMOOTH, PMG_OP_LSOLVE, PMG_OP_USOLVE, PMG_OP_RESTRICT, PMG_OP_PROLONG_ADD,

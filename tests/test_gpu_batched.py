@@ -70,7 +70,7 @@ def _relres(O, f, u, u0):
     return np.linalg.norm(O.residual(0, f, u)) / np.linalg.norm(O.residual(0, f, u0))
 
 
-CASES = [(0, 3, 5, 0), (1, 2, 5, 0), (2, 2, 3, 0), (0, 4, 6, 1)]
+CASES = [(0, 3, 5, 0), (1, 2, 5, 0), (2, 2, 3, 0), (0, 4, 6, 1), (3, 3, 5, 0)]
 
 
 @pytest.mark.parametrize("case", CASES)

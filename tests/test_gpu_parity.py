@@ -54,7 +54,8 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-SMALL = [(0, 3, 5, 0, 0), (0, 3, 5, 1, 0), (1, 2, 5, 0, 0), (2, 2, 3, 0, 0), (0, 4, 6, 0, 1), (2, 3, 4, 1, 0)]
+SMALL = [(0, 3, 5, 0, 0), (0, 3, 5, 1, 0), (1, 2, 5, 0, 0), (2, 2, 3, 0, 0), (0, 4, 6, 0, 1), (2, 3, 4, 1, 0),
+         (3, 3, 5, 0, 0)]
 
 
 @pytest.mark.parametrize("case", SMALL)

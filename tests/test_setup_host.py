@@ -56,6 +56,8 @@ CASES = [
     (1, 2, 5, 0, 0),   # unit square
     (2, 2, 3, 0, 0),   # unit cube
     (0, 4, 6, 0, 1),   # annulus, paper's benchmark-1 solution
+    (3, 3, 5, 0, 0),   # benchmark 2: convection-diffusion-reaction, unit square
+    (3, 2, 4, 1, 0),
 ]
 
 
