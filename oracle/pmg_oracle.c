@@ -12,7 +12,7 @@
  * threaded, in FP64, with no blocking, fusion or reordering beyond what the
  * definitions state.  Citations name the paper's section / equation / table.
  *
- * Readings of passages the paper leaves open (each also listed in the design doc):
+ * Readings of passages the paper leaves open:
  *   R1  Open uniform knots with span h = 2^-k, p+1 repeated end knots (Sec. 2).
  *   R2  DOF numbering: lexicographic, first parametric direction fastest,
  *       0-based (the index formula printed in Sec. 2 is garbled).
@@ -46,6 +46,9 @@
  *       interpolation P_c; restriction P_c^T; rediscretised operators.
  *   R13 Residual norm: Euclidean norm of the interior residual, relres =
  *       ||r_k|| / ||r_0||, checked after each V-cycle; divergence if > 1e10.
+ *   R14 Benchmark 2 (Sec. 2 gives the strong form): a_ij = int (D grad phi_j)
+ *       . grad phi_i + (v . grad phi_j) phi_i + R phi_j phi_i, phi_i the test
+ *       function (row); the P1 levels rediscretise the same equation.
  *
  * Parity status: every routine has a pin in tests/ except that the V-cycle as
  * a whole is pinned only softly (iteration counts of Table 4 within +-2,
