@@ -189,7 +189,9 @@ enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_FP16 = 2, PMG_PREC_
  * defect-correction loop; the outer residual, the update of u and the p = 1
  * coarse correction stay FP64.  F_dev, U0_dev, U_dev: nrhs x n[0] doubles,
  * right-hand side k contiguous at offset k*n[0] (device).  The workspace must
- * have been created with max_rhs >= max(nrhs, 2) (batched buffers).  iters_host[k]: cycles of
+ * have been created with max_rhs >= max(nrhs, 2) (batched buffers); the solve
+ * runs on the workspace's continuous-batching slots (pmg_slots_*), releasing
+ * all of them before and after, so slot work in progress on it is cancelled.  iters_host[k]: cycles of
  * right-hand side k; hist_host (may be NULL): max_iter x nrhs relative
  * residuals, row = cycle.  Blocks until done.  Errors: PMG_ERR_ARG,
  * PMG_ERR_MAXITER / PMG_ERR_DIVERGED (results still written), PMG_ERR_TIMEOUT,
