@@ -10,6 +10,7 @@
 #include <cstring>
 #include <queue>
 #include <stdexcept>
+#include <thread>
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -864,6 +865,14 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
   const int d = H.d, ne = 1 << k;
   const int nlev = (opt.projection == PMG_PROJ_DIRECT) ? 1 : p - 1;
   H.lev.resize(size_t(nlev));
+  std::vector<std::thread> workers;
+  struct JoinAll {   // every exit path waits for the level threads
+    std::vector<std::thread>& t;
+    ~JoinAll() { for (auto& x : t) if (x.joinable()) x.join(); }
+  } join_all{workers};
+  std::vector<pmg_status> wst(static_cast<size_t>(nlev), PMG_OK);
+  std::vector<std::string> werr(static_cast<size_t>(nlev));
+  std::vector<double> wms(static_cast<size_t>(nlev), 0.0);
   try {
     for (int l = 0; l < nlev; ++l) {
       PLevel& L = H.lev[size_t(l)];
@@ -899,21 +908,39 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
       }
       L.ML = lumped_mass(dom, d, ne, L.q);
       H.t_assembly += ms_since(t0);
-      t0 = clk::now();
-      pmg_status st = ilut_factor(L.A, opt.drop_tol, opt.fill_factor, L.L, L.U, L.udiag, err);
-      if (st != PMG_OK) return st;
-      L.depthL = critical_path(L.L, true);
-      L.depthU = critical_path(L.U, false);
-      L.Lsplit = line_split(L.L, L.n1d);
-      L.Um = mirror(L.U);
-      L.Umsplit = line_split(L.Um, L.n1d);
-      L.Llp = build_lp(L.L, L.n1d, nullptr, 4, 8);
-      {
-        std::vector<double> ud(size_t(L.N));
-        for (int i = 0; i < L.N; ++i) ud[size_t(i)] = 1.0 / L.udiag[size_t(L.N - 1 - i)];
-        L.Ulp = build_lp(L.Um, L.n1d, &ud, 4, 8);
+      // The ILUT factor of each level (a sequential row recurrence) and its
+      // solve layouts run on a thread of their own while the next level is
+      // assembled; every thread writes only its own level.
+      workers.emplace_back([&, l] {
+        PLevel& Lw = H.lev[size_t(l)];
+        const auto tw = clk::now();
+        try {
+          wst[size_t(l)] = ilut_factor(Lw.A, opt.drop_tol, opt.fill_factor, Lw.L, Lw.U, Lw.udiag, werr[size_t(l)]);
+          if (wst[size_t(l)] != PMG_OK) return;
+          Lw.depthL = critical_path(Lw.L, true);
+          Lw.depthU = critical_path(Lw.U, false);
+          Lw.Lsplit = line_split(Lw.L, Lw.n1d);
+          Lw.Um = mirror(Lw.U);
+          Lw.Umsplit = line_split(Lw.Um, Lw.n1d);
+          Lw.Llp = build_lp(Lw.L, Lw.n1d, nullptr, 4, 8);
+          std::vector<double> ud(size_t(Lw.N));
+          for (int i = 0; i < Lw.N; ++i) ud[size_t(i)] = 1.0 / Lw.udiag[size_t(Lw.N - 1 - i)];
+          Lw.Ulp = build_lp(Lw.Um, Lw.n1d, &ud, 4, 8);
+        } catch (const std::bad_alloc&) {
+          wst[size_t(l)] = PMG_ERR_OOM;
+          werr[size_t(l)] = "host allocation failed";
+        }
+        wms[size_t(l)] = ms_since(tw);
+      });
+    }
+    for (auto& w : workers) w.join();
+    workers.clear();
+    for (int l = 0; l < nlev; ++l) {
+      H.t_ilut = std::max(H.t_ilut, wms[size_t(l)]);     // concurrent: the longest level
+      if (wst[size_t(l)] != PMG_OK) {
+        err = werr[size_t(l)];
+        return wst[size_t(l)];
       }
-      H.t_ilut += ms_since(t0);
     }
     auto t0 = clk::now();
     H.ML1 = lumped_mass(dom, d, ne, 1);
