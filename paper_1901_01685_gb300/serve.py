@@ -235,6 +235,60 @@ class Server:
         self.used = 0
 
 
+class Router:
+    """Requests over several servers, one per GPU (the solves are independent:
+    no collective, host-side routing only).  A key stays on the server that
+    took it first, where its hierarchy is resident; a new key goes to the
+    server with the fewest right-hand sides outstanding.  Same interface as
+    Server (submit, step, pending_work, drain, close)."""
+
+    def __init__(self, servers: List[Server]):
+        assert servers, "a router needs at least one server"
+        self.servers = servers
+        self.home: Dict[Key, int] = {}
+
+    def _load(self, i: int) -> int:
+        srv = self.servers[i]
+        queued = sum(r.nrhs for q in srv.queue.values() for r in q)
+        running = sum(1 for ks in srv.keys.values() for rid in ks.slot_req if rid is not None)
+        return queued + running
+
+    def submit(self, req: Request, now: Optional[float] = None) -> Request:
+        if req.key not in self.home:
+            self.home[req.key] = min(range(len(self.servers)), key=self._load)
+        return self.servers[self.home[req.key]].submit(req, now)
+
+    def pending_work(self) -> bool:
+        return any(s.pending_work() for s in self.servers)
+
+    def step(self, now: Optional[float] = None) -> List[Request]:
+        done: List[Request] = []
+        for srv in self.servers:
+            done += srv.step(now)
+        return done
+
+    @property
+    def cycles(self) -> int:
+        return sum(s.cycles for s in self.servers)
+
+    @property
+    def evictions(self) -> int:
+        return sum(s.evictions for s in self.servers)
+
+    def drain(self, idle_sleep: float = 2e-4) -> List[Request]:
+        done: List[Request] = []
+        while self.pending_work():
+            got = self.step()
+            done += got
+            if not got:
+                time.sleep(idle_sleep)
+        return done
+
+    def close(self):
+        for srv in self.servers:
+            srv.close()
+
+
 def run_stream(server: Server, requests: List[Request], arrivals: np.ndarray, idle_sleep: float = 1e-4) -> dict:
     """Feeds `requests` at the given arrival offsets (seconds from start) and
     serves until all are done.  Returns latency percentiles and throughput."""

@@ -165,3 +165,23 @@ def test_poisson_arrivals_are_seeded_and_have_the_requested_rate():
     assert np.array_equal(a, b) and np.all(np.diff(a) > 0)
     mean_gap = a[-1] / len(a)
     assert abs(mean_gap - 1 / 50.0) < 4 * (1 / 50.0) / np.sqrt(len(a))   # 4 standard errors of the mean
+
+
+def test_router_keeps_keys_on_one_server_and_balances_new_keys():
+    """Several GPUs: each key lives on one server (no request of a key runs
+    elsewhere); new keys go to the least-loaded server; every result is right."""
+    keys = [(0, 2, 5), (0, 3, 5), (1, 2, 5), (1, 3, 5), (2, 2, 3)]
+    backends = [FakeBackend({k: 10 for k in keys}, budget=100) for _ in range(2)]
+    router = serve.Router([serve.Server(b, slots=8) for b in backends])
+    reqs = [_req(i, keys[i % len(keys)], 1 + i % 3, 2 + i % 4) for i in range(25)]
+    for r in reqs:
+        router.submit(r, now=0.0)
+    now = 0.0
+    while router.pending_work():
+        now += 1.0
+        router.step(now)
+    assert all(r.status == "done" and np.array_equal(r.U, 2 * r.F) for r in reqs)
+    served = [{l[0] for l in b.loads} for b in backends]
+    assert served[0].isdisjoint(served[1]) and served[0] | served[1] == set(keys)
+    assert all(served), "both servers took keys"
+    assert router.cycles > 0
