@@ -1,6 +1,7 @@
 /*
  * pmg.h -- C-ABI of the GB300 ILUT-smoothed p-multigrid solver for Galerkin
- * IgA discretisations of Poisson's equation.
+ * IgA discretisations of Poisson's equation (and the paper's
+ * convection-diffusion-reaction benchmark).
  *
  * Method: Tielen, Moeller, Goeddeke, Vuik, "A p-multigrid method enhanced with
  * an ILUT smoother and its comparison to h-multigrid methods within
@@ -22,10 +23,12 @@
  *    cudaStream_t passed as void* (NULL = legacy default stream).
  *  - The library allocates no device memory.  The hierarchy is copied into
  *    a caller-provided device arena (pmg_upload) and each solve uses a
- *    caller-provided device workspace (pmg_workspace_create).
- *  - A handle is immutable after pmg_upload and may be shared by concurrent
- *    solves that use different workspaces.  A workspace serves one solve at
- *    a time.
+ *    caller-provided device workspace (pmg_workspace_create); a workspace
+ *    for several right-hand sides also holds a small pinned host buffer.
+ *  - A handle's data is immutable after pmg_upload and may be shared by
+ *    concurrent solves that use different workspaces; only its kernel choice
+ *    changes (pmg_autotune, pmg_set_kernels), never while a solve uses it.
+ *    A workspace serves one solve at a time.
  */
 #ifndef PMG_H_
 #define PMG_H_
@@ -45,7 +48,7 @@ typedef enum {
   PMG_ERR_MAXITER = 5,    /* max_iter V-cycles without reaching rel_tol */
   PMG_ERR_TIMEOUT = 6,    /* a bounded device-side wait expired; results invalid */
   PMG_ERR_CUDA = 7,       /* a CUDA runtime call failed */
-  PMG_ERR_BUSY = 8,       /* reserved for admission control */
+  PMG_ERR_BUSY = 8,       /* slot call while a cycle is pending, or load into an active slot */
   PMG_ERR_STATE = 9       /* call out of order (e.g. solve before upload) */
 } pmg_status;
 
@@ -191,9 +194,11 @@ enum { PMG_PREC_FP64 = 0, PMG_PREC_MIXED = 1, PMG_PREC_MIXED_FP16 = 2, PMG_PREC_
  * right-hand side k contiguous at offset k*n[0] (device).  The workspace must
  * have been created with max_rhs >= max(nrhs, 2) (batched buffers); the solve
  * runs on the workspace's continuous-batching slots (pmg_slots_*), releasing
- * all of them before and after, so slot work in progress on it is cancelled.  iters_host[k]: cycles of
- * right-hand side k; hist_host (may be NULL): max_iter x nrhs relative
- * residuals, row = cycle.  Blocks until done.  Errors: PMG_ERR_ARG,
+ * all of them before and after, so slot work in progress on it is cancelled.
+ * iters_host[k]: cycles of right-hand side k; hist_host (may be NULL):
+ * max_iter x nrhs relative residuals, row = cycle.  On a non-default stream
+ * with profiling off, the cycles after the first are replayed as one CUDA
+ * graph.  Blocks until done.  Errors: PMG_ERR_ARG,
  * PMG_ERR_MAXITER / PMG_ERR_DIVERGED (results still written), PMG_ERR_TIMEOUT,
  * PMG_ERR_CUDA. */
 pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F_dev, const double* U0_dev,
@@ -213,8 +218,9 @@ pmg_status pmg_solve_batched(pmg_handle h, pmg_ws ws, int nrhs, const double* F_
  *   (none of them active), computes their initial residual norms and makes
  *   them active (a slot with a zero initial residual is reported converged
  *   with 0 cycles after the next cycle's wait).
- * pmg_slots_cycle: one V-cycle (PMG_PREC_FP64 or PMG_PREC_MIXED, as in
- *   pmg_solve_batched) for every active slot, then each one's stopping test
+ * pmg_slots_cycle: one V-cycle (precision as in pmg_solve_batched; replayed
+ *   as a CUDA graph on a non-default stream) for every active slot, then each
+ *   one's stopping test
  *   (relative residual < rel_tol: converged; > 1e10: diverged).  A no-op when
  *   no slot is active.
  * pmg_slots_wait: when the last cycle has finished (at once if
@@ -294,7 +300,7 @@ enum {
   PMG_K_RESIDUAL = 0,     /* r = f - A u on a p-level */
   PMG_K_TRANSFER = 1,     /* restriction / prolongation SpMV between p-levels */
   PMG_K_LSOLVE = 2,       /* forward substitution with the ILUT factor L */
-  PMG_K_USOLVE = 3,       /* backward substitution with U, fused u += e */
+  PMG_K_USOLVE = 3,       /* backward substitution with U (and u += e) */
   PMG_K_GS = 4,           /* Gauss-Seidel sweep on a P1 level */
   PMG_K_P1 = 5,           /* P1 residual and canonical transfers */
   PMG_K_COARSE = 6,       /* dense coarsest solve */
