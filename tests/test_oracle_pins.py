@@ -189,6 +189,116 @@ def test_lumped_projection_keeps_constants(oracle_mod, dom, k, q, r):
     assert np.abs(Pt @ np.ones(P.shape[0]) / mlc - 1).max() < 1e-13
 
 
+def _knots(q, ne):
+    """Open uniform knot vector of degree q with ne elements on [0, 1] (Sec. 2)."""
+    return np.array([0.0] * (q + 1) + [i / ne for i in range(1, ne)] + [1.0] * (q + 1))
+
+
+def _basis_integrals(q, ne, moment=False):
+    """Closed forms for an open uniform knot vector t: the integral of B_{a,q}
+    is (t_{a+q+1} - t_a) / (q + 1), and B_{a,q} divided by it is a probability
+    density whose mean is the average of its q + 2 knots t_a .. t_{a+q+1}, so
+    the first moment is that integral times the knot average."""
+    t = _knots(q, ne)
+    n = ne + q
+    w = np.array([(t[a + q + 1] - t[a]) / (q + 1) for a in range(n)])
+    if moment:
+        w = w * np.array([t[a:a + q + 2].mean() for a in range(n)])
+    return w
+
+
+@pytest.mark.parametrize("dom,p,k", [(0, 3, 3), (0, 4, 4), (1, 3, 4), (1, 2, 3), (2, 2, 3)])
+def test_lumped_mass_is_basis_integral(oracle_mod, dom, p, k):
+    """M^L_ii = integral of Phi_i over the domain (row sums over all columns,
+    boundary included, reading R6), checked against the closed-form integrals
+    of the B-splines for every degree level and for the P1 space: on the square
+    and cube a product of 1-D integrals; on the quarter annulus |det J| =
+    (pi/2)(1 + xi) with xi the first parametric direction, so the xi factor is
+    the integral of (1 + xi) B(xi)."""
+    O = oracle_mod
+    H = O.Hierarchy(dom, p, k)
+    ne = 1 << k
+    d = 3 if dom == 2 else 2
+    for lev in range(H.nlev + 1):
+        q = p - lev if lev < H.nlev else 1
+        w0 = _basis_integrals(q, ne)[1:-1]
+        wx = w0 + _basis_integrals(q, ne, moment=True)[1:-1] if dom == 0 else w0
+        full = wx
+        for _ in range(d - 1):
+            full = np.kron(w0, full)          # first direction fastest
+        if dom == 0:
+            full = full * (math.pi / 2)
+        ml = H.lumped_mass(lev)
+        assert ml.shape == full.shape
+        assert np.abs(ml - full).max() <= 1e-14 * np.abs(full).max(), (lev, np.abs(ml - full).max())
+
+
+def _design(q, ne, x):
+    """Values of the ne + q B-splines of degree q at the points x (scipy's own
+    B-spline evaluation, independent of the oracle's Cox-de Boor code)."""
+    from scipy.interpolate import BSpline
+    return BSpline.design_matrix(np.clip(x, 0.0, 1.0), _knots(q, ne), q).toarray()
+
+
+def _interp_interior(q, ne, g1d):
+    """Interior coefficients of the 1-D spline interpolant of g1d (g1d vanishes
+    at 0 and 1) at the Greville abscissae."""
+    t = _knots(q, ne)
+    n = ne + q
+    xs = np.array([t[i + 1:i + q + 1].mean() for i in range(n)])
+    c = np.linalg.solve(_design(q, ne, xs), g1d(xs))
+    return c[1:-1]
+
+
+def _l2_param_error(q, ne, coef_int, g1d, lo=0.375, hi=0.625):
+    """L2 norm over the parametric window [lo, hi]^2 of (spline with the given
+    interior coefficients, zero boundary coefficients) - g1d(xi) g1d(eta), by
+    5-point Gauss rules per element (lo and hi fall on element boundaries)."""
+    gx, gw = np.polynomial.legendre.leggauss(5)
+    pts = np.concatenate([(e + (gx + 1) / 2) / ne for e in range(ne)])
+    wts = np.concatenate([gw / (2 * ne)] * ne)
+    keep = (pts > lo) & (pts < hi)
+    pts, wts = pts[keep], wts[keep]
+    B = _design(q, ne, pts)[:, 1:-1]
+    n = B.shape[1]
+    val = B @ coef_int.reshape(n, n).T @ B.T          # val[a, b] at (xi_a, eta_b)
+    ref = np.outer(g1d(pts), g1d(pts))
+    return math.sqrt(float(np.einsum("a,b,ab->", wts, wts, (val - ref) ** 2)))
+
+
+@pytest.mark.parametrize("dom,p,lev", [(0, 3, 0), (0, 3, 1), (1, 4, 0), (1, 2, 0)])
+def test_lumped_transfers_converge_at_second_order(oracle_mod, dom, p, lev):
+    """The lumped L2 projections of Sec. 3 (Eq. prolongation, Eq. restriction)
+    map a smooth function's spline interpolant between the degree-q and the
+    coarser space with an O(h^2) error.  Prolongation of the coarse
+    interpolant and restriction of the fine one of g = sin(pi xi) sin(pi eta)
+    (zero on the boundary) are evaluated with scipy's B-splines.  Away from
+    the boundary the basis functions are symmetric, a lumped average is exact
+    for linear functions there, and the L2 error on the window [3/8, 5/8]^2
+    must fall at rate >= 2 - 0.2 from h = 2^-4 to 2^-7.  (Over the whole
+    domain the rate is 1.5: the open knot vector's asymmetric B-splines make
+    an O(h) error in a strip of width O(h) at the boundary; the exact
+    lumped-mass pin above covers those rows.)  A dropped or misplaced scaling,
+    a wrong transfer matrix or a wrong index breaks the rate."""
+    O = oracle_mod
+    g1d = lambda s: np.sin(np.pi * s)
+    errs_p, errs_r = [], []
+    for k in (4, 5, 6, 7):
+        ne = 1 << k
+        H = O.Hierarchy(dom, p, k)
+        q = p - lev
+        qc = q - 1 if lev + 1 < H.nlev else 1
+        cq = np.kron(_interp_interior(q, ne, g1d), _interp_interior(q, ne, g1d))
+        cc = np.kron(_interp_interior(qc, ne, g1d), _interp_interior(qc, ne, g1d))
+        up = H.prolong_add(lev, cc, np.zeros(H.N[lev]))
+        rc = H.restrict(lev, cq)
+        errs_p.append(_l2_param_error(q, ne, up, g1d))
+        errs_r.append(_l2_param_error(qc, ne, rc, g1d))
+    for errs in (errs_p, errs_r):
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+        assert min(rates) > 2 - 0.2, (errs_p, errs_r)
+
+
 def _greville_coeffs(O, q, ne, g1d):
     n = ne + q
     # Greville abscissae of the open uniform knot vector
