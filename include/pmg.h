@@ -102,10 +102,13 @@ typedef struct {
   double cycle_bytes;                   /* algorithmic DRAM bytes of one V-cycle */
   double cycle_flops;                   /* floating-point operations of one V-cycle */
   /* kernel variant of each solve (0 windowed line-pipelined, 1 ring, 2 lines
-   * per CTA), two bits each.  tune_p[l]: single-vector forward, backward;
-   * batched FP64 forward, backward; batched FP32 forward, backward.
-   * tune_h[j]: single-vector forward, backward sweep; batched forward,
-   * backward sweep. */
+   * per CTA, 3 chain and producers on a two-CTA cluster), two bits each.
+   * tune_p[l]: single-vector forward, backward; batched FP64 forward,
+   * backward; batched FP32 forward, backward; then the chain configuration
+   * (0..3: producer sums enter the chain in groups of 1, 2, 4, 8 rows) of the
+   * clustered kernel for the forward and the backward solve.  tune_h[j]: single-vector
+   * forward, backward sweep; batched forward, backward sweep; chain
+   * configuration of the forward and the backward sweep. */
   int tune_p[PMG_MAX_LEVELS];
   int tune_h[PMG_MAX_LEVELS];
 } pmg_info_t;
@@ -254,9 +257,9 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream);
 
 /* Sets the kernel variant of every solve by hand, in the packing of
  * pmg_info_t.tune_p / tune_h (arrays of nlevels / nhlevels ints): single-vector
- * solves and sweeps take 0 or 1, batched ones 1 or 2.  The hierarchy must be
- * uploaded.  Errors: PMG_ERR_ARG (a variant out of range; nothing changed),
- * PMG_ERR_STATE. */
+ * solves and sweeps take 0, 1 or 3, batched ones 1 or 2; chain configurations
+ * 0..3.  The hierarchy must be uploaded.  Errors: PMG_ERR_ARG (a variant out of
+ * range; nothing changed), PMG_ERR_STATE. */
 pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h);
 
 /* Single steps of the cycle, for checking each one on its own.  `level` is a
@@ -335,8 +338,10 @@ pmg_status pmg_ws_stats(pmg_ws ws, pmg_stats_t* out, int reset);
  * device array of this library, present on every GPU that loads it until the
  * process exits, which limits n to 1,048,576 rows (4 MiB of scratch).
  *   n: rows; rp_dev (n+1), ci_dev, v_dev: CSR arrays of L on the device, columns
- *   ascending, all < their row; b_dev: right-hand side; y_dev: output (may not
- *   alias b_dev).  All device memory is owned by the caller.
+ *   ascending, all < their row (a column outside [0, row) is not checked and
+ *   gives undefined results); ci_dev and v_dev must be non-null even when L
+ *   has no entries; b_dev: right-hand side; y_dev: output (may not alias
+ *   b_dev).  All device memory is owned by the caller.
  * The first call on a device looks up the array's device address (with that
  * device current); make that first call before any stream capture.  Every call
  * shares the one array and clears the part it uses; calls whose work overlaps

@@ -119,14 +119,21 @@ struct DevPLevel {
 // Kernel variant of each solve: the line-pipelined windowed kernel (single
 // vectors), the ring kernel, or the lines-per-CTA kernel (batched).  Defaults
 // are the measured best on GB300; pmg_autotune re-measures them.
-enum : unsigned char { kVarLp2 = 0, kVarRing = 1, kVarLines = 2 };
+enum : unsigned char { kVarLp2 = 0, kVarRing = 1, kVarLines = 2, kVarCluster = 3 };
+// Chain configurations of the clustered kernel k_lp4: producer sums enter the
+// chain in groups of G rows, A+1 .. A+G rows ahead.
+struct Lp4Cfg { int G, A; };
+constexpr Lp4Cfg kLp4Cfgs[] = {{1, 1}, {2, 1}, {4, 1}, {8, 1}};
+constexpr int kNumLp4Cfgs = 4;
 struct PTune {
-  unsigned char sL = kVarLp2, sU = kVarLp2;           // single vector: forward / backward ILUT solve
+  unsigned char sL = kVarCluster, sU = kVarCluster;   // single vector: forward / backward ILUT solve
+  unsigned char cL = 1, cU = 1;                       // k_lp4 chain configuration (index into kLp4Cfgs)
   unsigned char bL[2] = {kVarRing, kVarRing};         // batched, [0] FP64, [1] FP32
   unsigned char bU[2] = {kVarRing, kVarRing};
 };
 struct HTune {
   unsigned char gF = kVarRing, gB = kVarRing;         // single vector: forward / backward sweep
+  unsigned char cF = 1, cB = 1;                       // k_lp4 chain configuration of the sweeps
   unsigned char bF = kVarRing, bB = kVarRing;         // batched
 };
 
@@ -225,6 +232,13 @@ struct pmg_workspace_s {
   long long prof_n[PMG_NKERN] = {0};
   double prof_bytes[PMG_NKERN] = {0};
   long long launches = 0;
+  // first failed stream-ordered runtime call (fill, copy) since the last check;
+  // finish_launches reports it by name
+  cudaError_t async_err = cudaSuccess;
+  const char* async_what = nullptr;
+  void note(cudaError_t e, const char* what) {
+    if (e != cudaSuccess && async_err == cudaSuccess) { async_err = e; async_what = what; }
+  }
   ~pmg_workspace_s() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (slot_ev) cudaEventDestroy(slot_ev);
@@ -388,7 +402,7 @@ double csr_bytes(long long nnz, int nr) { return 12.0 * double(nnz) + 4.0 * (nr 
 
 unsigned* next_counter(Ctx& c) {
   if (c.w->next_slot >= kCounterSlots) {
-    cudaMemsetAsync(c.w->counters, 0, kCounterSlots * sizeof(unsigned), c.s);
+    c.w->note(cudaMemsetAsync(c.w->counters, 0, kCounterSlots * sizeof(unsigned), c.s), "reset of the launch counters");
     c.w->next_slot = 0;
   }
   return c.w->counters + c.w->next_slot++;
@@ -399,7 +413,7 @@ unsigned next_epoch(Ctx& c) {
     int maxN = 0;
     for (const auto& L : H.lev) maxN = std::max(maxN, L.N);
     for (const auto& Hl : H.hl) maxN = std::max(maxN, Hl.N);
-    cudaMemsetAsync(c.w->flags, 0, size_t(maxN) * sizeof(unsigned), c.s);
+    c.w->note(cudaMemsetAsync(c.w->flags, 0, size_t(maxN) * sizeof(unsigned), c.s), "reset of the ready flags");
     c.w->epoch = 1u;
   }
   return c.w->epoch;
@@ -423,10 +437,60 @@ bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double*
   const int grid = std::max(1, std::min(nblocks, c.h->sms));
   unsigned* cnt = next_counter(c);
   // the output starts as "pending" (all-ones bytes); rows publish by overwriting it
-  cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s);
+  c.w->note(cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s), "pending fill of a solve's output");
   pmgk::k_lp2<MIR, UPD, WIN, LPR><<<grid, 32 * (pmgk::kLpProducers + 1) * pmgk::kLpLinesPerCta, smem, c.s>>>(
       M, b, x, u, cnt, c.w->err);
   return true;
+}
+
+// Chain/producer split over two-CTA clusters (k_lp4), chain configuration G, A.
+template <bool MIR, bool UPD, int WIN, int LPR, int G, int A>
+bool lp4_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double* u) {
+  const size_t smem = (size_t((M.nx + 1) & ~1) + size_t(3) * pmgk::kLpStage * 32) * sizeof(double);
+  if (smem > kLpSmemCap) return false;
+  const void* fn = (const void*)pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A>;
+  allow_smem(fn);
+  const int clusters = std::max(1, std::min(M.nlines, c.h->sms / 2));
+  unsigned* cnt = next_counter(c);
+  // the output starts as "pending" (all-ones bytes); rows publish by overwriting it
+  c.w->note(cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s), "pending fill of a solve's output");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * clusters);
+  cfg.blockDim = dim3(32 * pmgk::kLp4Warps);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  pmgk::Lp2 m = M;
+  c.w->note(cudaLaunchKernelEx(&cfg, pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A>, m, b, x, u, cnt, c.w->err),
+            "cluster launch of the line-pipelined solve");
+  return true;
+}
+template <bool MIR, bool UPD, int WIN, int LPR>
+bool lp4_launch_c(Ctx& c, int cfg, const pmgk::Lp2& M, const double* b, double* x, double* u) {
+  switch (cfg) {
+    case 0: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[0].G, kLp4Cfgs[0].A>(c, M, b, x, u);
+    case 1: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[1].G, kLp4Cfgs[1].A>(c, M, b, x, u);
+    case 2: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[2].G, kLp4Cfgs[2].A>(c, M, b, x, u);
+    case 3: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[3].G, kLp4Cfgs[3].A>(c, M, b, x, u);
+    default: return false;
+  }
+}
+// Layouts the setup builds: ILUT factors (4 rows x 8 lanes; forward, or
+// mirrored backward with or without the update), P1 sweeps (4 rows x 4 lanes).
+bool lp4_launch(Ctx& c, int cfg, const pmgk::Lp2& M, bool mirror, const double* b, double* x, double* u) {
+  if (M.win == 4 && M.lpr == 8) {
+    if (!mirror) return u ? false : lp4_launch_c<false, false, 4, 8>(c, cfg, M, b, x, u);
+    return u ? lp4_launch_c<true, true, 4, 8>(c, cfg, M, b, x, u) : lp4_launch_c<true, false, 4, 8>(c, cfg, M, b, x, u);
+  }
+  if (M.win == 4 && M.lpr == 4 && !u)
+    return mirror ? lp4_launch_c<true, false, 4, 4>(c, cfg, M, b, x, u) : lp4_launch_c<false, false, 4, 4>(c, cfg, M, b, x, u);
+  return false;
 }
 
 template <int WIN, int LPR>
@@ -485,7 +549,7 @@ bool b_lpc(Ctx& c, int cls, const pmgk::LpC<T, CT>& M, long long nnz, bool mirro
   // algorithmic bytes: each factor entry once (column index + value at the
   // storage precision), row pointers, b read and x written
   launch(c, cls, (4.0 + sizeof(CT)) * nnz + 4.0 * (M.n + 1) + 2.0 * M.n * R * sizeof(T), [&] {
-    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
+    c.w->note(cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s), "pending fill of a solve's output");
     pmgk::LpC<T, CT> m = M;
     int r = R;
     const T* bb = b;
@@ -507,6 +571,7 @@ void lsolve(Ctx& c, int l, const double* b, double* y) {
   if (c.h->ptune[l].sL == kVarRing && b_lpc<double>(c, PMG_K_LSOLVE, D.Lc64, D.nnzL, false, b, y, 1, D.inflightL))
     return;
   launch(c, PMG_K_LSOLVE, csr_bytes(D.nnzL, D.N) + 16.0 * D.N, [&] {
+    if (c.h->ptune[l].sL == kVarCluster && lp4_launch(c, c.h->ptune[l].cL, D.Llp, false, b, y, nullptr)) return;
     if (lp_launch(c, D.Llp, false, b, y, nullptr)) return;
     const unsigned ep = next_epoch(c);
     unsigned* cnt = next_counter(c);
@@ -520,6 +585,7 @@ void usolve(Ctx& c, int l, const double* y, double* e, double* u) {
     return;
   }
   launch(c, PMG_K_USOLVE, csr_bytes(D.nnzU, D.N) + (u ? 40.0 : 24.0) * D.N, [&] {
+    if (c.h->ptune[l].sU == kVarCluster && lp4_launch(c, c.h->ptune[l].cU, D.Ulp, true, y, e, u)) return;
     if (lp_launch(c, D.Ulp, true, y, e, u)) return;
     const unsigned ep = next_epoch(c);
     unsigned* cnt = next_counter(c);
@@ -555,7 +621,9 @@ void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   }
   launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
     spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms);
-    if (lp_launch(c, backward ? D.UpMlp : D.Lolp, backward, t, xn, nullptr)) {
+    const pmgk::Lp2& lay = backward ? D.UpMlp : D.Lolp;
+    const int cfg = backward ? c.h->htune[j].cB : c.h->htune[j].cF;
+    if ((var == kVarCluster && lp4_launch(c, cfg, lay, backward, t, xn, nullptr)) || lp_launch(c, lay, backward, t, xn, nullptr)) {
       cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
       return;
     }
@@ -674,6 +742,12 @@ pmg_status begin_launches(Ctx& c) {
 }
 
 pmg_status finish_launches(Ctx& c) {
+  if (c.w->async_err != cudaSuccess) {
+    const std::string msg = std::string(c.w->async_what) + " failed: " + cudaGetErrorString(c.w->async_err);
+    c.w->async_err = cudaSuccess;
+    cudaGetLastError();
+    return fail(PMG_ERR_CUDA, msg);
+  }
   PMG_CUDA(cudaGetLastError());
   unsigned errw[4] = {0, 0, 0, 0};
   PMG_CUDA(cudaMemcpyAsync(errw, c.w->err, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c.s));
@@ -855,7 +929,7 @@ void b_lp(Ctx& c, int cls, const pmgk::LpB<T>& M, long long nnz, bool mirror, co
   const int grid = std::max(1, std::min(nitems, 2 * c.h->sms));
   unsigned* cnt = next_counter(c);
   launch(c, cls, 12.0 * nnz + 4.0 * (M.n + 1) + (u ? 4.0 : 2.0) * M.n * R * sizeof(T), [&] {
-    cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s);
+    c.w->note(cudaMemsetAsync(x, 0xFF, size_t(M.n) * R * sizeof(T), c.s), "pending fill of a solve's output");
     const int th = 32 * lines;
     const int k = (mirror ? 2 : 0) + (u ? 1 : 0);
     if (k == 0) { allow_smem((const void*)pmgk::k_lpb<T, false, false>); pmgk::k_lpb<T, false, false><<<grid, th, smem, c.s>>>(M, R, b, x, u, cnt, c.w->err); }
@@ -1369,11 +1443,12 @@ pmg_status pmg_info(pmg_handle h, pmg_info_t* info) {
   info->cycle_flops = flops;
   for (size_t l = 0; l < H.lev.size(); ++l) {
     const PTune t = l < h->ptune.size() ? h->ptune[l] : PTune{};
-    info->tune_p[l] = t.sL | (t.sU << 2) | (t.bL[0] << 4) | (t.bU[0] << 6) | (t.bL[1] << 8) | (t.bU[1] << 10);
+    info->tune_p[l] = t.sL | (t.sU << 2) | (t.bL[0] << 4) | (t.bU[0] << 6) | (t.bL[1] << 8) | (t.bU[1] << 10) |
+                      (t.cL << 12) | (t.cU << 14);
   }
   for (size_t j = 0; j < H.hl.size(); ++j) {
     const HTune t = j < h->htune.size() ? h->htune[j] : HTune{};
-    info->tune_h[j] = t.gF | (t.gB << 2) | (t.bF << 4) | (t.bB << 6);
+    info->tune_h[j] = t.gF | (t.gB << 2) | (t.bF << 4) | (t.bB << 6) | (t.cF << 8) | (t.cB << 10);
   }
   return PMG_OK;
 }
@@ -1709,16 +1784,31 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
     }
     slot = arg;
   };
+  // single-vector solves and sweeps: the windowed kernel, the ring kernel and
+  // every chain configuration of the clustered kernel
+  auto pick_single = [&](unsigned char& var, unsigned char& cfg, bool ring_ok, auto&& fn) {
+    double best = 1e300;
+    unsigned char bv = var, bc = cfg;
+    auto trial = [&](unsigned char v, unsigned char k) {
+      var = v;
+      cfg = k;
+      const double t = timeit(fn);
+      if (t < best) { best = t; bv = v; bc = k; }
+    };
+    trial(kVarLp2, cfg);
+    if (ring_ok) trial(kVarRing, cfg);
+    for (int k = 0; k < kNumLp4Cfgs; ++k) trial(kVarCluster, (unsigned char)k);
+    var = bv;
+    cfg = bc;
+  };
   const size_t cap = kLpSmemCap;
   for (size_t l = 0; l < h->dl.size() && err == PMG_OK; ++l) {
     const DevPLevel& D = h->dl[l];
     const int L = int(l);
     fill(ws->f[l], D.N);
     const bool ring_ok = size_t(D.Lc64.nx + 64) * 32 * sizeof(double) <= cap;
-    if (ring_ok) {
-      pick(h->ptune[l].sL, {kVarLp2, kVarRing}, [&] { lsolve(c, L, ws->f[l], ws->y[l]); });
-      pick(h->ptune[l].sU, {kVarLp2, kVarRing}, [&] { usolve(c, L, ws->f[l], ws->e[l], nullptr); });
-    }
+    pick_single(h->ptune[l].sL, h->ptune[l].cL, ring_ok, [&] { lsolve(c, L, ws->f[l], ws->y[l]); });
+    pick_single(h->ptune[l].sU, h->ptune[l].cU, ring_ok, [&] { usolve(c, L, ws->f[l], ws->e[l], ws->u[l]); });
     if (ws->R) {
       const long long nR = (long long)D.N * ws->R;
       double* b64 = ws->bf[l];
@@ -1739,8 +1829,9 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
     const int J = int(j);
     fill(ws->hb[j], D.N);
     fill(ws->hx[j], D.N);
-    pick(h->htune[j].gF, {kVarLp2, kVarRing}, [&] { gs(c, J, false, ws->hb[j], ws->hx[j]); });
-    pick(h->htune[j].gB, {kVarLp2, kVarRing}, [&] { gs(c, J, true, ws->hb[j], ws->hx[j]); });
+    const bool ring_ok = size_t(D.Loc.nx + 64) * 32 * sizeof(double) <= cap;
+    pick_single(h->htune[j].gF, h->htune[j].cF, ring_ok, [&] { gs(c, J, false, ws->hb[j], ws->hx[j]); });
+    pick_single(h->htune[j].gB, h->htune[j].cB, ring_ok, [&] { gs(c, J, true, ws->hb[j], ws->hx[j]); });
     if (ws->R) {
       const long long nR = (long long)D.N * ws->R;
       fill(ws->bhb[j], nR);
@@ -1760,16 +1851,18 @@ pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
   if (!h || !tune_p || !tune_h) return fail(PMG_ERR_ARG, "null argument");
   if (!h->uploaded) return fail(PMG_ERR_STATE, "hierarchy not uploaded");
   auto field = [](int v, int k) { return (unsigned char)((v >> (2 * k)) & 3); };
+  auto single_ok = [](unsigned char f) { return f != kVarLines; };
+  auto batched_ok = [](unsigned char f) { return f == kVarRing || f == kVarLines; };
   for (size_t l = 0; l < h->dl.size(); ++l) {
     const int v = tune_p[l];
-    if (field(v, 0) > kVarRing || field(v, 1) > kVarRing) return fail(PMG_ERR_ARG, "single-vector solves take variant 0 or 1");
+    if (!single_ok(field(v, 0)) || !single_ok(field(v, 1)))
+      return fail(PMG_ERR_ARG, "single-vector solves take variant 0, 1 or 3");
     for (int k = 2; k < 6; ++k)
-      if (field(v, k) == kVarLp2) return fail(PMG_ERR_ARG, "batched solves take variant 1 or 2");
+      if (!batched_ok(field(v, k))) return fail(PMG_ERR_ARG, "batched solves take variant 1 or 2");
   }
   for (size_t j = 0; j < h->dh.size(); ++j) {
     const int v = tune_h[j];
-    if (field(v, 0) > kVarRing || field(v, 1) > kVarRing || field(v, 2) == kVarLp2 || field(v, 3) == kVarLp2 ||
-        field(v, 2) > kVarLines || field(v, 3) > kVarLines)
+    if (!single_ok(field(v, 0)) || !single_ok(field(v, 1)) || !batched_ok(field(v, 2)) || !batched_ok(field(v, 3)))
       return fail(PMG_ERR_ARG, "invalid sweep variant");
   }
   for (size_t l = 0; l < h->dl.size(); ++l) {
@@ -1777,11 +1870,13 @@ pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
     PTune& t = h->ptune[l];
     t.sL = field(v, 0); t.sU = field(v, 1);
     t.bL[0] = field(v, 2); t.bU[0] = field(v, 3); t.bL[1] = field(v, 4); t.bU[1] = field(v, 5);
+    t.cL = field(v, 6); t.cU = field(v, 7);
   }
   for (size_t j = 0; j < h->dh.size(); ++j) {
     const int v = tune_h[j];
     HTune& t = h->htune[j];
     t.gF = field(v, 0); t.gB = field(v, 1); t.bF = field(v, 2); t.bB = field(v, 3);
+    t.cF = field(v, 4); t.cB = field(v, 5);
   }
   ++h->tune_epoch;
   return PMG_OK;
@@ -2004,7 +2099,8 @@ pmg_status noalloc_device(NoAllocDevice** out) {
 
 extern "C" pmg_status pmg_lsolve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* v_dev,
                                          const double* b_dev, double* y_dev, void* stream) {
-  if (n < 0 || (n > 0 && (!rp_dev || !b_dev || !y_dev))) return fail(PMG_ERR_ARG, "invalid argument");
+  if (n < 0 || (n > 0 && (!rp_dev || !ci_dev || !v_dev || !b_dev || !y_dev)))
+    return fail(PMG_ERR_ARG, "pmg_lsolve_noalloc: negative n or a null device pointer");
   if (n > kNoAllocMaxRows)
     return fail(PMG_ERR_ARG, "pmg_lsolve_noalloc: n = " + std::to_string(n) + " exceeds the fixed scratch limit of " +
                                  std::to_string(kNoAllocMaxRows) + " rows");

@@ -77,10 +77,11 @@ CASES = [(0, 3, 5), (1, 2, 5), (2, 2, 3)]
 
 
 @pytest.mark.parametrize("case", CASES)
-@pytest.mark.parametrize("single,sweep", [(0, 0), (1, 1), (0, 1), (1, 0)])
-def test_single_vector_variants_match_oracle(torch_mod, pmg, oracle_mod, case, single, sweep):
+@pytest.mark.parametrize("single,sweep,cfg", [(0, 0, 0), (1, 1, 0), (0, 1, 0), (1, 0, 0),
+                                              (3, 3, 0), (3, 3, 1), (3, 3, 2), (3, 3, 3), (3, 1, 2)])
+def test_single_vector_variants_match_oracle(torch_mod, pmg, oracle_mod, case, single, sweep, cfg):
     S, O = _pair(pmg, oracle_mod, *case)
-    S.set_kernels(single=single, sweep_single=sweep)
+    S.set_kernels(single=single, sweep_single=sweep, chain_cfg=cfg)
     _check_single(torch_mod, S, O)
 
 
@@ -97,7 +98,7 @@ def test_autotuned_kernels_match_oracle(torch_mod, pmg, oracle_mod, case):
     S, O = _pair(pmg, oracle_mod, *case)
     kp, kh = S.autotune()
     assert len(kp) == O.nlev and len(kh) == O.nh
-    assert all(v in ("windowed", "ring") for d in kp for k, v in d.items() if k.startswith("single"))
+    assert all(v in ("windowed", "ring", "cluster") for d in kp for k, v in d.items() if k.startswith("single"))
     assert all(v in ("ring", "lines") for d in kp for k, v in d.items() if k.startswith("batched"))
     _check_single(torch_mod, S, O)
     _check_batched(torch_mod, pmg, S, O)
@@ -106,7 +107,7 @@ def test_autotuned_kernels_match_oracle(torch_mod, pmg, oracle_mod, case):
 def test_set_kernels_rejects_invalid_variants(torch_mod, pmg, oracle_mod):
     S, O = _pair(pmg, oracle_mod, 1, 2, 5)
     before = S.info["kernels_p"]
-    for tp, th in (([2] * O.nlev, [0] * O.nh),            # single-vector solve variant 2
+    for tp, th in (([2 | (1 << 4) | (1 << 6) | (1 << 8) | (1 << 10)] * O.nlev, [0] * O.nh),  # single-vector variant 2
                    ([0] * O.nlev, [0] * O.nh)):           # batched variant 0 (single-vector kernel)
         with pytest.raises(pmg.PmgError) as e:
             pmg.pmg_set_kernels(S.h, tp, th)

@@ -23,16 +23,25 @@ def torch_mod():
 
 
 def test_noalloc_lsolve_matches_workspace_path(torch_mod):
+    """Two calls in a row through the C-ABI, each compared with the library's
+    workspace-based forward solve (PMG_OP_LSOLVE) and with scipy's triangular
+    solve on the CPU oracle's own ILUT factor L (unit diagonal)."""
     torch = torch_mod
+    import scipy.sparse
+    import scipy.sparse.linalg
+    from oracle import oracle as O
     from paper_1901_01685_gb300 import pmg
     S = pmg.Solver(pmg.PMG_QUARTER_ANNULUS, 3, 6)
     n, _, rp, ci, v = pmg.pmg_export_csr(S.h, 1, 0)
+    Lo = O.Hierarchy(O.ANNULUS, 3, 6).csr("L", 0)
+    Lu = scipy.sparse.csr_matrix((Lo.v, Lo.ci, Lo.rp), shape=(n, n)) + scipy.sparse.identity(n, format="csr")
     rp_d = torch.as_tensor(rp, device="cuda")
     ci_d = torch.as_tensor(ci, device="cuda")
     v_d = torch.as_tensor(v, device="cuda")
     rng = np.random.default_rng(21)
     for call in range(2):  # two calls in a row: the shared scratch must not leak state
-        b = torch.as_tensor(rng.standard_normal(n), device="cuda")
+        bh = rng.standard_normal(n)
+        b = torch.as_tensor(bh, device="cuda")
         y_ref = torch.empty(n, dtype=torch.float64, device="cuda")
         S.apply(pmg.PMG_OP_LSOLVE, 0, None, b, y_ref)
         y = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
@@ -40,6 +49,9 @@ def test_noalloc_lsolve_matches_workspace_path(torch_mod):
         torch.cuda.synchronize()
         err = (y - y_ref).abs().max().item() / max(y_ref.abs().max().item(), 1e-300)
         assert err <= TOL, (call, err)
+        y_cpu = scipy.sparse.linalg.spsolve_triangular(Lu, bh, lower=True)
+        err_o = np.abs(y.cpu().numpy() - y_cpu).max() / np.abs(y_cpu).max()
+        assert err_o <= TOL, (call, err_o)
 
 
 def test_noalloc_rejects_sizes_above_its_limit(torch_mod):
