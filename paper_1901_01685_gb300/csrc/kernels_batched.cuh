@@ -287,11 +287,123 @@ __device__ __forceinline__ void lds_row(const double* p, double (&c)[NC]) {
   }
 }
 
-template <class T>
-__device__ __forceinline__ T lpc_wait_filled(volatile T* p, unsigned* err, unsigned site, int item, int row) {
-  T v = *p;
-  if (!Pending<T>::is(v)) return v;
-  return lpb_wait<T, true>(const_cast<const T*>(p), err, site, item, row);
+// Warp-uniform wait: every lane's value at p (shared memory when SHARED,
+// else a relaxed global load) until no lane of the warp has one pending.
+// All lanes loop together; a per-lane spin would leave the warp split into
+// thread groups that issue every later instruction separately (measured
+// several times slower on GB300).
+template <class T, bool SHARED>
+__device__ __noinline__ T lpc_wait_uniform(const T* p, T v, unsigned* err, unsigned site, int item, int row) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (Pending<T>::is(v)) v = SHARED ? *reinterpret_cast<const volatile T*>(p) : ld_relaxed_t<T>(p);
+    if (!__any_sync(0xffffffffu, Pending<T>::is(v))) return v;
+    if (!SHARED) __nanosleep(it < 16 ? 32u : 256u);
+    if ((it & 31u) == 31u) {
+      const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+      if (__any_sync(0xffffffffu, expired)) {
+        if (Pending<T>::is(v)) {
+          wait_expired(err, site, item, row);
+          v = T(0);
+        }
+        return v;
+      }
+    }
+  }
+}
+
+// Producer warp pw of k_lpc: rows pw, pw + P, ... of the line; for each,
+// s_i = d_i b_i - sum_far d_i M_ij x_j, handed to the chain with the row's
+// ring coefficients through hand-over slot (i mod 32).  Called out of line:
+// inlined into the kernel, producer code made the compiler emit a slower
+// chain loop.
+template <class T, bool MIRROR, int RING, class CT>
+__device__ __noinline__ void lpc_producer(LpC<T, CT> M, int R, const T* __restrict__ b, T* x, volatile T* xs,
+                                          volatile T* sb, T* cb, int row0, int col, int item, int pw, int lane,
+                                          unsigned* err) {
+  constexpr int NC = RING - 1;
+  constexpr int BATCH = sizeof(T) == 4 ? 32 : 16;
+  const int nx = M.nx;
+  for (int ix = pw; ix < nx; ix += LpcProducers<T>::value) {
+    const int i = row0 + ix;
+    const size_t o = (size_t)lp_vec<MIRROR>(i, M.n) * R + col;
+    const T bi = M.dscale ? b[o] * __ldg(M.dscale + i) : b[o];
+    const T cf = lane < NC ? (T)coef_ld(M.push + (size_t)i * 32 + lane) : T(0);
+    const int beg = __ldg(M.frp + i), end = __ldg(M.frp + i + 1);
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int t0 = beg; t0 < end; t0 += BATCH) {
+      int jj[BATCH];
+      T cv[BATCH], xv[BATCH];
+#pragma unroll
+      for (int q = 0; q < BATCH; ++q) {
+        const int t = t0 + q;
+        jj[q] = t < end ? __ldg(M.fci + t) : -1;
+        cv[q] = t < end ? (T)coef_ld(M.fv + t) : T(0);
+      }
+      // Issue every load of the batch first (own line from shared memory,
+      // earlier lines with relaxed loads at GPU scope, which read L2: x is
+      // written during this kernel), then wait, warp-uniformly, for the
+      // pending ones.
+      bool pend = false;
+#pragma unroll
+      for (int q = 0; q < BATCH; ++q) {
+        const int j = jj[q];
+        xv[q] = T(0);
+        if (j >= row0) xv[q] = xs[(size_t)(j - row0) * 32 + lane];
+        else if (j >= 0) xv[q] = ld_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col);
+        pend |= Pending<T>::is(xv[q]);
+      }
+      if (__any_sync(0xffffffffu, pend)) {
+        const long long tw = clock64();
+        for (unsigned it = 0;; ++it) {
+          pend = false;
+#pragma unroll
+          for (int q = 0; q < BATCH; ++q)
+            if (Pending<T>::is(xv[q])) {
+              const int j = jj[q];
+              xv[q] = j >= row0 ? xs[(size_t)(j - row0) * 32 + lane]
+                                : ld_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col);
+              pend |= Pending<T>::is(xv[q]);
+            }
+          if (!__any_sync(0xffffffffu, pend)) break;
+          __nanosleep(it < 16 ? 32u : 256u);
+          if ((it & 31u) == 31u) {
+            const bool expired = ld_relaxed(err) != 0u || clock64() - tw > kWaitCycles;
+            if (__any_sync(0xffffffffu, expired)) {
+              if (pend) wait_expired(err, kSiteGlobal, item, ix);
+#pragma unroll
+              for (int q = 0; q < BATCH; ++q)
+                if (Pending<T>::is(xv[q])) xv[q] = T(0);
+              break;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < BATCH; ++q) a[q & 3] = fma(cv[q], xv[q], a[q & 3]);
+    }
+    const T s = bi - ((a[0] + a[1]) + (a[2] + a[3]));
+    volatile T* slot = sb + (ix & 31) * 32 + lane;
+    // wait, warp-uniformly, for the chain to have taken row ix - 32 out of
+    // every lane's slot (bounded)
+    const long long t0 = clock64();
+    for (unsigned it = 0; __any_sync(0xffffffffu, !Pending<T>::is(*slot)); ++it) {
+      if ((it & 31u) == 31u) {
+        const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+        if (__any_sync(0xffffffffu, expired)) {
+          if (lane == 0) wait_expired(err, kSiteSlotFree, item, ix);
+          break;
+        }
+      }
+    }
+    // The chain's lane L reads the coefficients of all lanes: every
+    // coefficient is written before any lane publishes s.
+    __syncwarp();
+    cb[(ix & 31) * 32 + lane] = cf;
+    __syncwarp();
+    __threadfence_block();
+    *slot = s;
+  }
 }
 
 template <class T, bool MIRROR, int RING, class CT = T>
@@ -299,7 +411,6 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
                                                                    unsigned* counter, unsigned* err) {
   static_assert(RING >= 2 && RING <= 32 && (RING & (RING - 1)) == 0, "ring must be a power of two <= 32");
   constexpr int NC = RING - 1;
-  constexpr int BATCH = sizeof(T) == 4 ? 32 : 16;
   extern __shared__ __align__(16) unsigned char lpc_smem[];
   using PU = typename Pending<T>::U;
   volatile T* xs = reinterpret_cast<volatile T*>(lpc_smem);   // [nx][32] values of the line
@@ -322,99 +433,42 @@ __global__ void __launch_bounds__(32 * (1 + LpcProducers<T>::value)) k_lpc(LpC<T
     if (item >= nitems) return;
     const int line = item / G, g = item % G;
     const int row0 = line * nx, col = single ? 0 : g * 32 + lane;
-    if (warp == 0) {
-      T acc[RING];
+    if (warp != 0) {
+      lpc_producer<T, MIRROR, RING, CT>(M, R, b, x, xs, sb, cb, row0, col, item, warp - 1, lane, err);
+      continue;
+    }
+    // ------------------------------- chain -------------------------------
+    T acc[RING];
 #pragma unroll
-      for (int k = 0; k < RING; ++k) acc[k] = T(0);
-      for (int i0 = 0; i0 < nx; i0 += 32) {
+    for (int k = 0; k < RING; ++k) acc[k] = T(0);
+    for (int i0 = 0; i0 < nx; i0 += 32) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int ix = i0 + k;
-          if (ix < nx) {
-            volatile T* slot = sb + k * 32 + lane;
-            const T s = lpc_wait_filled(slot, err, kSiteSlotFilled, item, ix);
-            __threadfence_block();              // the row's coefficients were written before s
-            T c[NC];
-            lds_row<NC>(cb + k * 32, c);
-            const int a0 = k & (RING - 1);
-            T xv = s - acc[a0];
-            if (Pending<T>::is(xv)) xv = Pending<T>::other_nan();   // never publish the marker
-            acc[a0] = T(0);
+      for (int k = 0; k < 32; ++k) {
+        const int ix = i0 + k;
+        if (ix < nx) {
+          volatile T* slot = sb + k * 32 + lane;
+          T s = *slot;
+          if (__any_sync(0xffffffffu, Pending<T>::is(s)))
+            s = lpc_wait_uniform<T, true>(const_cast<const T*>(slot), s, err, kSiteSlotFilled, item, ix);
+          __threadfence_block();              // the row's coefficients were written before s
+          T c[NC];
+          lds_row<NC>(cb + k * 32, c);
+          const int a0 = k & (RING - 1);
+          T xv = s - acc[a0];
+          if (Pending<T>::is(xv)) xv = Pending<T>::other_nan();   // never publish the marker
+          acc[a0] = T(0);
 #pragma unroll
-            for (int m = 1; m < RING; ++m) acc[(k + m) & (RING - 1)] = fma(c[m - 1], xv, acc[(k + m) & (RING - 1)]);
-            // the pushes consumed c: release the slot to its producer
-            *reinterpret_cast<volatile PU*>(slot) = Pending<T>::bits;
-            xs[(size_t)ix * 32 + lane] = xv;
-            st_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(row0 + ix, M.n) * R + col, xv);
-          }
+          for (int m = 1; m < RING; ++m) acc[(k + m) & (RING - 1)] = fma(c[m - 1], xv, acc[(k + m) & (RING - 1)]);
+          // the pushes consumed c: release the slot to its producer
+          *reinterpret_cast<volatile PU*>(slot) = Pending<T>::bits;
+          xs[(size_t)ix * 32 + lane] = xv;
+          st_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(row0 + ix, M.n) * R + col, xv);
         }
-      }
-    } else {
-      const int pw = warp - 1;
-      for (int ix = pw; ix < nx; ix += LpcProducers<T>::value) {
-        const int i = row0 + ix;
-        const size_t o = (size_t)lp_vec<MIRROR>(i, M.n) * R + col;
-        const T bi = M.dscale ? b[o] * __ldg(M.dscale + i) : b[o];
-        const T cf = lane < NC ? (T)coef_ld(M.push + (size_t)i * 32 + lane) : T(0);
-        const int beg = __ldg(M.frp + i), end = __ldg(M.frp + i + 1);
-        T a[4] = {T(0), T(0), T(0), T(0)};
-        for (int t0 = beg; t0 < end; t0 += BATCH) {
-          int jj[BATCH];
-          T cv[BATCH], xv[BATCH];
-#pragma unroll
-          for (int q = 0; q < BATCH; ++q) {
-            const int t = t0 + q;
-            jj[q] = t < end ? __ldg(M.fci + t) : -1;
-            cv[q] = t < end ? (T)coef_ld(M.fv + t) : T(0);
-          }
-          // Issue every load of the batch first, then resolve the pending ones
-          // (own line from shared memory, earlier lines with relaxed loads at
-          // GPU scope, which read L2: x is written during this kernel).
-#pragma unroll
-          for (int q = 0; q < BATCH; ++q) {
-            const int j = jj[q];
-            xv[q] = T(0);
-            if (j >= row0) xv[q] = xs[(size_t)(j - row0) * 32 + lane];
-            else if (j >= 0) xv[q] = ld_relaxed_t<T>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col);
-          }
-#pragma unroll
-          for (int q = 0; q < BATCH; ++q) {
-            if (Pending<T>::is(xv[q])) {
-              const int j = jj[q];
-              xv[q] = j >= row0 ? lpc_wait_filled(xs + (size_t)(j - row0) * 32 + lane, err, kSiteShared, item, ix)
-                                : lpb_wait<T, false>(x + (size_t)lp_vec<MIRROR>(j, M.n) * R + col, err,
-                                                     kSiteGlobal, item, ix);
-            }
-          }
-#pragma unroll
-          for (int q = 0; q < BATCH; ++q) a[q & 3] = fma(cv[q], xv[q], a[q & 3]);
-        }
-        const T s = bi - ((a[0] + a[1]) + (a[2] + a[3]));
-        volatile T* slot = sb + (ix & 31) * 32 + lane;
-        // wait for the chain to have taken row ix - 32 out of this slot (bounded)
-        const long long t0 = clock64();
-        for (unsigned it = 0; !Pending<T>::is(*slot); ++it) {
-          if ((it & 31u) == 31u && (ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles)) {
-            wait_expired(err, kSiteSlotFree, item, ix);
-            break;
-          }
-        }
-        // The chain's lane L reads the coefficients of all lanes but waits
-        // only for slot lane L, so the warp converges twice: every lane's slot
-        // has been released (row ix - 32 fully consumed) before any lane
-        // overwrites the row's coefficients, and every coefficient is written
-        // before any lane publishes s.
-        __syncwarp();
-        cb[(ix & 31) * 32 + lane] = cf;
-        __syncwarp();
-        __threadfence_block();
-        *slot = s;
       }
     }
   }
 }
 
-// P1 canonical transfers, batched ([node][R]).
 __global__ void k_p1_restrict_b(int d, int nf, int R, const double* __restrict__ rf, double* __restrict__ rc) {
   const int nc = nf / 2, mc = nc - 1, mf = nf - 1;
   const long long Nc = (d == 2) ? (long long)mc * mc : (long long)mc * mc * mc;
