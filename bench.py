@@ -31,12 +31,25 @@ METRIC = "MDOF*iter/s to 1e-8 relres (plain FP64)"
 UNIT = "MDOF*iter/s"
 DEGREES = (2, 3, 4, 5)
 LOG2H = 8
-SERVING_KEYS = [(d, p, k) for d in (0, 1) for k in (5, 6, 7) for p in (2, 3, 4, 5)] + [(2, 2, 4), (2, 3, 4)]
-SERVING_REQUESTS = 256
+# served keys: {quarter annulus, unit square} x h = 2^-5..2^-8 x p = 2..5, and the
+# unit cube at h = 2^-5 with p = 2, 3 (p = 4, 5 of the cube left out: their host
+# setup alone takes minutes)
+SERVING_KEYS = [(d, p, k) for d in (0, 1) for k in (5, 6, 7, 8) for p in (2, 3, 4, 5)] + [(2, 2, 5), (2, 3, 5)]
+SERVING_REQUESTS = 512
 SERVING_SLOTS = 32
+SERVING_ORACLE_SAMPLE = 12   # served requests re-checked by the oracle (keys with h >= 2^-7)
 BATCHED_CASE = (0, 4, 9)     # quarter annulus, p = 4, h = 2^-9
 BATCHED_NRHS = 64
+CUBE_DEGREES = (2, 3)
+CUBE_NRHS = 32
+CUBE_REFS = 4                # seeded right-hand sides the oracle also solves per cube degree
+CUBE_STEPS = 3
+SECTION_STEPS = 5            # timed repetitions of the extra sections' forms
 WORKLOAD = "quarter annulus Poisson, h=2^-8, p=2..5, indirect p-MG V-cycle, ILUT(1e-12,1), 1e-8 relres"
+# The clustered triangular-solve kernel's chain warp resolves one row per ~96 ns
+# in steady state (GB300 at 2070 MHz, from a traced run of the forward solve at
+# h = 2^-8, p = 3): the per-row floor of the solves' critical path.
+CHAIN_ROW_NS = 96.0
 
 
 def _env_int(name, default):
@@ -159,6 +172,86 @@ def _oracle_sample(budget_s: float, degrees=DEGREES):
     return units / secs / 1e6, secs, steps
 
 
+def _host_info() -> dict:
+    """Core count and CPU model of the host the CPU legs run on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": os.uname().machine}
+
+
+def _oracle_references(case, nrhs: int, threads: int, seeds=(2, 1)):
+    """CPU leg: the FP64 oracle's solutions of the seeded right-hand sides of a
+    case (inputs.batched_rhs with seed seeds[0], initial guess seed seeds[1];
+    nrhs == 1 means the assembled load vector itself), solved by a pool of
+    `threads` host threads on one oracle hierarchy (its solves only read it).
+    Returns the solutions, cycle counts, setup and solve seconds."""
+    import concurrent.futures
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1901_01685_gb300 import inputs
+    t = time.perf_counter()
+    H = O.Hierarchy(*case)
+    setup_s = time.perf_counter() - t
+    f = H.rhs()
+    F = f[None, :] if nrhs == 1 else inputs.batched_rhs(f, nrhs, seed=seeds[0])
+    u0 = inputs.initial_guess(H.N[0], seeds[1])
+    t = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(lambda r: H.solve(F[r], u0), range(F.shape[0])))
+    solve_s = time.perf_counter() - t
+    return {"U": np.stack([r[0] for r in res]), "iters": [int(r[2]) for r in res],
+            "status": [r[3] for r in res], "setup_s": setup_s, "solve_s": solve_s, "threads": threads}
+
+
+def _oracle_cube_refs(p: int):
+    """CPU leg: the oracle's solutions for the cube section at degree p (the
+    load vector, and the first CUBE_REFS seeded right-hand sides), one setup."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1901_01685_gb300 import inputs
+    H = O.Hierarchy(O.CUBE, p, 5)
+    f = H.rhs()
+    u0 = inputs.initial_guess(H.N[0], 1)
+    single = H.solve(f, u0)
+    F = inputs.batched_rhs(f, CUBE_REFS, seed=2)
+    batched = [H.solve(F[r], u0) for r in range(CUBE_REFS)]
+    return ({"U": single[0][None, :], "iters": [int(single[2])]},
+            {"U": np.stack([b[0] for b in batched]), "iters": [int(b[2]) for b in batched]})
+
+
+def _oracle_check_served(samples, threads: int):
+    """CPU leg: relative residuals ||f - A u|| / ||f - A u0|| of served results,
+    recomputed with the oracle's operator of each request's key.  samples: list
+    of (key, F, U0, U) with right-hand sides as rows."""
+    import concurrent.futures
+    import numpy as np
+    from oracle import oracle as O
+    keys = sorted({s[0] for s in samples})
+    with concurrent.futures.ThreadPoolExecutor(min(threads, len(keys))) as ex:
+        hier = dict(zip(keys, ex.map(lambda k: O.Hierarchy(*k), keys)))
+    out = []
+    for key, F, U0, U in samples:
+        H = hier[key]
+        for r in range(F.shape[0]):
+            num = np.linalg.norm(H.residual(0, F[r], U[r]))
+            den = np.linalg.norm(H.residual(0, F[r], U0[r]))
+            out.append(num / den)
+    return {"keys": [list(k) for k in keys], "results": len(out), "max_relres": float(max(out)),
+            "median_relres": float(np.median(out))}
+
+
 def run_reference(args):
     """The reference arm: the oracle (there is no reference implementation),
     one host thread, the same workload and step as the GPU arm (one solve per
@@ -276,7 +369,7 @@ def _batched_section(args, dist, flush, stream, world):
             for _ in range(args.warmup):
                 fn()
             ms, out = [], None
-            for _ in range(args.steps):
+            for _ in range(SECTION_STEPS):
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -286,7 +379,7 @@ def _batched_section(args, dist, flush, stream, world):
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
         stream.wait_stream(side)
-        return reduce_step_time(sum(ms) / 1e3, dist, "cuda") / args.steps, out
+        return reduce_step_time(sum(ms) / 1e3, dist, "cuda") / SECTION_STEPS, out
 
     u1 = torch.empty(N, dtype=torch.float64, device="cuda")
     t_single, single = timed(lambda: S.solve(F[0], U0[0], u=u1)[1])
@@ -329,9 +422,9 @@ def _batched_section(args, dist, flush, stream, world):
                      "MDOF_iter_per_s": world * N * int(np.sum(it)) / t / 1e6,
                      "iterations": [int(it.min()), int(it.max())], "u": U.clone(),
                      "graph_replays": gl["graph_launches"], "kernel_launches": gl["total_launches"]}
-    # the reduced-precision forms against the FP64 form (itself checked against
-    # the FP64 oracle by the tests): relative difference of the solutions and
-    # the FP64 relative residual of each result
+    # every form's FP64 relative residual, and the reduced-precision forms
+    # against the FP64 form; the error against the FP64 oracle is added once
+    # the CPU leg has the oracle's solutions (see run_ours)
     r0n = []
     for r in range(BATCHED_NRHS):
         r0 = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -346,9 +439,8 @@ def _batched_section(args, dist, flush, stream, world):
             S.apply(pmg.PMG_OP_RESIDUAL, 0, res[name]["u"][r], F[r], rr)
             rel.append(rr.norm().item() / r0n[r])
         errors[name] = {"max_rel_diff_u_vs_fp64": du.max().item(), "max_final_fp64_relres": max(rel)}
-    for v in res.values():
-        v.pop("u")
-    return {"workload": f"quarter annulus Poisson, h=2^-{k}, p={p}, {BATCHED_NRHS} right-hand sides "
+    sols = {name: v.pop("u").cpu().numpy() for name, v in res.items()}
+    return {"_sols": sols, "workload": f"quarter annulus Poisson, h=2^-{k}, p={p}, {BATCHED_NRHS} right-hand sides "
                         "(f scaled by U[0.5,2] plus 1% nodal noise), 1e-8 relres each",
             "dofs": N, "nrhs": BATCHED_NRHS, "l2_flush": "2x L2 write before every timed solve",
             "kernels": {"levels": S.info["kernels_p"], "p1_levels": S.info["kernels_h"]},
@@ -357,29 +449,152 @@ def _batched_section(args, dist, flush, stream, world):
             **res,
             "mixed_vs_plain_fp64_solves_per_s": res["mixed"]["solves_per_s"] * t_single / world,
             "mixed_vs_batched_fp64_solves_per_s": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"],
+            "target_readings": "mixed_vs_batched_fp64: the FP32-inner batched solve against the FP64 batched solve "
+                               "of the same right-hand sides; mixed_vs_plain_fp64: against plain FP64 solves one "
+                               "right-hand side at a time",
             "error_vs_fp64": errors,
             "bandwidth_kernels_cold_l2": bw}
+
+
+def _rel_err(U, Uref):
+    """Per-row relative 2-norm differences (numpy arrays, rows = right-hand sides)."""
+    import numpy as np
+    return np.linalg.norm(U - Uref, axis=1) / np.linalg.norm(Uref, axis=1)
+
+
+def _err_summary(e) -> dict:
+    import numpy as np
+    return {"max": float(np.max(e)), "median": float(np.median(e)), "results": int(len(e))}
+
+
+def _cube_section(args, dist, flush, world):
+    """Benchmark 4 of Sec. 2 (unit cube, homogeneous Dirichlet), h = 2^-5,
+    p = 2, 3: the plain FP64 V-cycle (single vector, and batched over 32 seeded
+    right-hand sides) against the FP32-inner cycle in FP64 defect correction
+    on the same right-hand sides.  The solutions are kept for the comparison
+    with the FP64 oracle's solutions of the same inputs (_cube_oracle_errors)."""
+    import numpy as np
+    import torch
+    from paper_1901_01685_gb300 import inputs, pmg
+    out = {"workload": "unit cube Poisson, f = 3 pi^2 sin sin sin, h=2^-5, p=2,3, indirect p-MG, 1e-8 relres; "
+                       f"batched forms over {CUBE_NRHS} right-hand sides (f scaled by U[0.5,2] plus 1% noise)",
+           "l2_flush": "2x L2 write before every timed solve"}
+    side = torch.cuda.Stream()
+    for p in CUBE_DEGREES:
+        S = pmg.Solver(pmg.PMG_UNIT_CUBE, p, 5, max_rhs=CUBE_NRHS)
+        if not args.no_autotune:
+            S.autotune()
+        N = S.N
+        f = torch.as_tensor(S.rhs(), device="cuda")
+        u0 = torch.as_tensor(inputs.initial_guess(N, 1), device="cuda")
+        F = torch.as_tensor(inputs.batched_rhs(S.rhs(), CUBE_NRHS, seed=2), device="cuda")
+        U0 = u0.expand(CUBE_NRHS, N).contiguous()
+        U = torch.empty_like(U0)
+        u = torch.empty_like(u0)
+        side.wait_stream(torch.cuda.current_stream())
+
+        def timed(fn):
+            with torch.cuda.stream(side):
+                for _ in range(args.warmup):
+                    fn()
+                ms, res = [], None
+                for _ in range(CUBE_STEPS):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(side)
+                    res = fn()
+                    e1.record(side)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+            return reduce_step_time(sum(ms) / 1e3, dist, "cuda") / CUBE_STEPS, res
+
+        t1, it1 = timed(lambda: S.solve(f, u0, u=u)[1])
+        entry = {"dofs": N, "single_fp64": {"ms_per_solve": 1e3 * t1, "MDOF_iter_per_s": world * N * it1 / t1 / 1e6,
+                                            "iterations": it1}}
+        sols = {"single_fp64": u.cpu().numpy()[None, :]}
+        for name, prec in (("batched_fp64", pmg.PMG_PREC_FP64), ("batched_mixed", pmg.PMG_PREC_MIXED)):
+            t, its = timed(lambda: S.solve_batched(F, U0, precision=prec, U=U)[1])
+            entry[name] = {"ms_per_batch": 1e3 * t, "solves_per_s": world * CUBE_NRHS / t,
+                           "MDOF_iter_per_s": world * N * int(np.sum(its)) / t / 1e6,
+                           "iterations": [int(its.min()), int(its.max())]}
+            sols[name] = U.cpu().numpy()
+        entry["mixed_vs_batched_fp64_solves_per_s"] = (entry["batched_mixed"]["solves_per_s"] /
+                                                      entry["batched_fp64"]["solves_per_s"])
+        entry["_sols"] = sols
+        out[f"p{p}"] = entry
+        del S
+    return out
+
+
+def _batched_oracle_errors(batched, ref):
+    """Adds each batched form's error against the FP64 oracle's solutions of the
+    same right-hand sides and the oracle's thread-pool timing (the host
+    baseline of this workload), then drops the raw solutions."""
+    sols = batched.pop("_sols", None)
+    if sols is None:
+        return
+    Uref = ref["U"]
+    batched["error_vs_fp64_oracle"] = {
+        name: _err_summary(_rel_err(U[:Uref.shape[0]], Uref)) for name, U in sols.items()}
+    batched["error_vs_fp64_oracle"]["note"] = ("relative 2-norm error of every GPU solution against the oracle's "
+                                               "solution of the same right-hand side, per form")
+    import numpy as np
+    batched["cpu_baseline_thread_pool"] = {
+        "kind": "oracle", "threads": ref["threads"], "solves": int(Uref.shape[0]),
+        "solves_per_s": Uref.shape[0] / ref["solve_s"],
+        "MDOF_iter_per_s": batched["dofs"] * int(np.sum(ref["iters"])) / ref["solve_s"] / 1e6,
+        "oracle_iterations": [int(min(ref["iters"])), int(max(ref["iters"]))],
+        "setup_s": ref["setup_s"],
+        "note": "the oracle (plain FP64 C) solving the same right-hand sides with a pool of host threads on one "
+                "hierarchy, setup excluded; run beside the GPU sections, so it shares the host with them"}
+
+
+def _cube_oracle_errors(cube, refs):
+    """Adds each cube form's error against the FP64 oracle (refs: degree ->
+    (single reference, batched references)) and drops the raw solutions."""
+    for p in CUBE_DEGREES:
+        entry = cube.get(f"p{p}")
+        if not isinstance(entry, dict) or "_sols" not in entry:
+            continue
+        sols = entry.pop("_sols")
+        single, batched = refs[p]
+        k = batched["U"].shape[0]
+        entry["error_vs_fp64_oracle"] = {
+            "single_fp64": _err_summary(_rel_err(sols["single_fp64"], single["U"])),
+            "batched_fp64": _err_summary(_rel_err(sols["batched_fp64"][:k], batched["U"])),
+            "batched_mixed": _err_summary(_rel_err(sols["batched_mixed"][:k], batched["U"])),
+            "oracle_iterations": single["iters"] + batched["iters"],
+            "note": f"relative 2-norm error of each GPU solution against the oracle's solution of the same inputs "
+                    f"(the load vector, and the first {k} seeded right-hand sides of the batched forms)"}
 
 
 def _serving_section(args):
     """Continuous-batching server: a seeded Poisson stream of requests over
     2D and 3D problem keys (1-16 right-hand sides each), served once with plain
     FP64 cycles and once with FP32-inner cycles, same arrivals; p50/p99
-    latency (arrival to result on the host) and solves/s.  Hierarchies are set
-    up and made resident before the stream starts (setup is timed separately,
-    as in the paper's App. C)."""
+    latency (arrival to result on the host), split into queueing (arrival to
+    load into slots) and service (load to result), and solves/s.  Hierarchies
+    are set up and made resident before the stream starts (setup is timed
+    separately, as in the paper's App. C).  Also the same requests solved
+    one at a time by plain FP64 single-vector solves, and a seeded sample of
+    served results kept for the oracle's check (returned under _oracle_sample)."""
     import numpy as np
-    from paper_1901_01685_gb300 import pmg, serve
+    from paper_1901_01685_gb300 import inputs, pmg, serve
     keys = SERVING_KEYS
     out = {"workload": f"{SERVING_REQUESTS} requests, keys uniform over {len(keys)} (domain, p, h): quarter "
-                       "annulus and unit square h=2^-5..2^-7, p=2..5; unit cube h=2^-4, p=2..3; 1-16 right-hand "
+                       "annulus and unit square h=2^-5..2^-8, p=2..5; unit cube h=2^-5, p=2..3; 1-16 right-hand "
                        "sides each, 1e-8 relres; saturation run (all requests at t=0, plain FP64), then Poisson "
                        "arrivals at 0.8x the saturation request rate, plain FP64 and FP32-inner, same arrivals",
-           "slots_per_key": SERVING_SLOTS}
-    be = serve.GpuBackend(autotune=not args.no_autotune)
+           "slots_per_key": SERVING_SLOTS,
+           "left_out": "unit cube p=4,5 at h=2^-5: host setup alone takes minutes (DESIGN.md)",
+           "kernels": "default variants (no autotuning of the served keys)"}
+    # default kernel variants (the measured best on GB300): autotuning every key
+    # would add minutes of setup
+    be = serve.GpuBackend(autotune=False)
     srv = serve.Server(be, slots=SERVING_SLOTS, precision=pmg.PMG_PREC_FP64)
     t0 = time.perf_counter()
-    srv.prewarm(keys)
+    srv.prewarm(keys, threads=min(16, os.cpu_count() or 4))
     out["setup_s"] = time.perf_counter() - t0
     rhs = {k: (srv.keys[k].handle["S"].rhs(), srv.keys[k].handle["S"].N) for k in keys}
 
@@ -391,12 +606,43 @@ def _serving_section(args):
     out["saturation_fp64"] = sat
     out["arrival_rate_per_s"] = rate
     arrivals = serve.poisson_arrivals(SERVING_REQUESTS, rate, seed=7)
+    served = None
     for name, prec in (("fp64", pmg.PMG_PREC_FP64), ("mixed", pmg.PMG_PREC_MIXED)):
         srv.precision = prec
         srv.cycles = 0
-        out[name] = serve.run_stream(srv, fresh(), arrivals)
-    srv.close()
+        served = fresh()
+        out[name] = serve.run_stream(srv, served, arrivals)
     out["mixed_vs_fp64_solves_per_s"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+
+    # the same requests, in arrival order, solved one right-hand side at a time
+    # by plain FP64 single-vector solves (bounded to ~10 s of solving)
+    import torch
+    one, t_one, n_one = fresh(), 0.0, 0
+    for idx in np.argsort(arrivals, kind="stable"):
+        req = one[idx]
+        S = srv.keys[req.key].handle["S"]
+        for r in range(req.nrhs):
+            f = torch.as_tensor(req.F[r], device="cuda")
+            u0 = torch.as_tensor(req.U0[r], device="cuda")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            S.solve(f, u0)
+            torch.cuda.synchronize()
+            t_one += time.perf_counter() - t
+            n_one += 1
+        if t_one > 10.0:
+            break
+    out["plain_fp64_one_at_a_time"] = {"solves": n_one, "solves_per_s": n_one / t_one,
+                                       "note": "the stream's requests in arrival order, each right-hand side by "
+                                               "a single-vector FP64 solve, no batching"}
+    out["mixed_served_vs_plain_fp64_one_at_a_time"] = out["mixed"]["solves_per_s"] / (n_one / t_one)
+    srv.close()
+    # seeded sample of served FP32-inner results on 2D keys with h >= 2^-7 for
+    # the oracle's check (its setups of those keys take seconds)
+    cand = [r for r in served if r.key[0] != pmg.PMG_UNIT_CUBE and r.key[2] <= 7 and r.status == "done"]
+    pick = inputs.uniform01(13, SERVING_ORACLE_SAMPLE)
+    chosen = sorted({min(int(u * len(cand)), len(cand) - 1) for u in pick}) if cand else []
+    out["_oracle_sample"] = [(tuple(cand[i].key), cand[i].F, cand[i].U0, cand[i].U) for i in chosen]
     return out
 
 
@@ -407,11 +653,18 @@ def run_ours(args):
     # The CPU baseline (oracle, one host core) builds its hierarchies and times
     # its sample in a spawned process while the GPU part runs; it is started
     # before the first GPU call.
-    cpu_job = pool = None
+    # The oracle's reference solutions for the cube and batched sections run
+    # there too (their setups take minutes on one core), in parallel workers.
+    cpu_job = pool = cube_refs = batched_ref = None
     if world == 1 and not args.no_cpu_baseline and not args.case:
         import multiprocessing
-        pool = multiprocessing.get_context("spawn").Pool(1)
+        ncpu = os.cpu_count() or 4
+        pool = multiprocessing.get_context("spawn").Pool(4)
         cpu_job = pool.apply_async(_oracle_sample, (args.cpu_budget,))
+        if not args.no_cube:
+            cube_refs = {p: pool.apply_async(_oracle_cube_refs, (p,)) for p in CUBE_DEGREES}
+        if not args.no_batched and not args.batched_case:
+            batched_ref = pool.apply_async(_oracle_references, (BATCHED_CASE, BATCHED_NRHS, max(1, ncpu - 6)))
     import numpy as np
     import torch
     from paper_1901_01685_gb300 import inputs, pmg
@@ -510,6 +763,18 @@ def run_ours(args):
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     total_ms = sum(c["ms"] for c in classes.values())
+    # critical path of the triangular-solve classes: solve depth (wavefronts of
+    # the factor's dependency graph, from the setup) x the chain's measured time
+    # per row, against the class's event-timed total; two solves per level and
+    # V-cycle of each kind (nu1 = nu2 = 1)
+    crit = {}
+    for cls, key in (("lsolve", "depth_L"), ("usolve", "depth_U")):
+        rows = sum(it * 2 * sum(S.info[key]) for S, it in zip(solvers, iters)) * args.steps
+        c = classes.get(cls)
+        if c and c["ms"]:
+            floor_ms = rows * CHAIN_ROW_NS * 1e-6
+            crit[cls] = {"depth_rows": rows, "row_floor_ns": CHAIN_ROW_NS, "floor_ms": floor_ms,
+                         "measured_ms": c["ms"], "frac": floor_ms / c["ms"]}
 
     # the same solves with BiCGSTAB preconditioned by the V-cycle (Sec. 5, Table 5)
     def bicg_section():
@@ -561,7 +826,13 @@ def run_ours(args):
     direct = None if args.no_direct or args.case else optional(
         lambda: _direct_section(args, dist, flush, stream, world))
     batched = None if args.no_batched else optional(lambda: _batched_section(args, dist, flush, stream, world))
+    cube = None if args.no_cube or args.case else optional(lambda: _cube_section(args, dist, flush, world))
     serving = None if args.no_serving or rank != 0 else optional(lambda: _serving_section(args))
+    served_check = None
+    if serving is not None and "_oracle_sample" in serving:
+        sample = serving.pop("_oracle_sample")
+        if pool is not None and sample:
+            served_check = pool.apply_async(_oracle_check_served, (sample, max(1, (os.cpu_count() or 4) - 2)))
 
     if rank != 0:
         return
@@ -573,11 +844,16 @@ def run_ours(args):
                    "iterations": iters, "parallelism": f"replicas{world}", "l2_flush": "2x L2 write between steps",
                    "kernels": [{"p": S.info["p"], "levels": S.info["kernels_p"], "p1_levels": S.info["kernels_h"]}
                                for S in solvers],
-                   "wall_s": wall},
+                   "wall_s": wall,
+                   "timing": "CUDA events per step on the launch stream; per-launch CUDA events around every "
+                             "kernel are also on in the timed region (they feed the roofline)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(dom),
                      "avg_launch_ms": avg_ms, "bytes_per_launch": bytes_per_launch,
-                     "share_of_kernel_time": dc["ms"] / total_ms if total_ms else None},
+                     "share_of_kernel_time": dc["ms"] / total_ms if total_ms else None,
+                     "critical_path": crit.get(dom) or crit,
+                     "note": "the triangular solves are bound by their dependency chain, not by HBM: "
+                             "critical_path.frac = depth x the chain's measured time per row / event time"},
         "kernel_classes": {k: {"ms": round(v["ms"], 3), "launches": v["launches"],
                                "GBps": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None}
                            for k, v in classes.items()},
@@ -593,18 +869,38 @@ def run_ours(args):
         line["direct_projection"] = direct
     if bicg is not None:
         line["bicgstab"] = bicg
+    def attach(what, fn):
+        # the oracle's checks never cost the contract line: a failure is reported in place
+        try:
+            fn()
+        except Exception as exc:  # noqa: BLE001
+            what["oracle_error"] = f"{type(exc).__name__}: {exc}"
+
     if batched is not None:
+        if batched_ref is not None and "_sols" in batched:
+            attach(batched, lambda: _batched_oracle_errors(batched, batched_ref.get(timeout=1200)))
+        batched.pop("_sols", None)
         line["batched"] = batched
+    if cube is not None:
+        if cube_refs is not None:
+            attach(cube, lambda: _cube_oracle_errors(cube, {p: r.get(timeout=1200) for p, r in cube_refs.items()}))
+        for p in CUBE_DEGREES:
+            if isinstance(cube.get(f"p{p}"), dict):
+                cube[f"p{p}"].pop("_sols", None)
+        line["cube"] = cube
     if serving is not None:
+        if served_check is not None:
+            attach(serving, lambda: serving.__setitem__("oracle_check", served_check.get(timeout=900)))
         line["serving"] = serving
     if cpu_job is not None:
+        host = _host_info()
         try:
             v, secs, steps = cpu_job.get(timeout=900)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host,
                                     "sample": f"{steps} steps of one oracle solve per degree p=2..5 at h=2^-8 "
                                               f"(the GPU arm's step), setup excluded, {secs:.1f} s of solving"}
         except Exception as exc:  # noqa: BLE001
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host,
                                     "error": f"{type(exc).__name__}: {exc}"}
         pool.close()
     print(json.dumps(line), flush=True)
@@ -625,6 +921,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the continuous-batching serving section")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-projection variant of the workload")
     ap.add_argument("--no-bicgstab", action="store_true", help="skip the BiCGSTAB timing of the workload")
+    ap.add_argument("--no-cube", action="store_true", help="skip the unit-cube FP64 / FP32-inner section")
     ap.add_argument("--batched-case", default="", help="dom,p,log2_inv_h of the many-right-hand-side section")
     ap.add_argument("--case", default="", help="dom,p,log2_inv_h: time one problem instead of the workload")
     args = ap.parse_args()

@@ -307,13 +307,22 @@ def run_stream(server: Server, requests: List[Request], arrivals: np.ndarray, id
         if not got:
             time.sleep(idle_sleep)
     t_end = time.perf_counter()
-    lat = np.array([r.latency for r in requests if r.latency is not None and r.status != "rejected"])
+    served = [r for r in requests if r.latency is not None and r.status != "rejected"]
+    lat = np.array([r.latency for r in served])
+    # queueing: arrival to the request's load into slots; service: load to result
+    queue = np.array([r.t_admitted - r.t_arrival for r in served if r.t_admitted is not None])
+    service = np.array([r.t_done - r.t_admitted for r in served if r.t_admitted is not None])
     solves = sum(r.nrhs for r in requests if r.status in ("done", "maxiter", "diverged"))
+
+    def pct(a, q):
+        return 1e3 * float(np.percentile(a, q)) if a.size else None
+
     return {"requests": len(requests), "completed": sum(r.status == "done" for r in requests),
             "rejected": sum(r.status == "rejected" for r in requests),
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
             "mean_ms": 1e3 * float(lat.mean()) if lat.size else None,
+            "queue_p50_ms": pct(queue, 50), "queue_p99_ms": pct(queue, 99),
+            "service_p50_ms": pct(service, 50), "service_p99_ms": pct(service, 99),
             "makespan_s": t_end - t0, "solves": solves, "solves_per_s": solves / (t_end - t0),
             "cycles": server.cycles, "evictions": server.evictions}
 
