@@ -311,7 +311,7 @@ namespace pmgk {
 // a bounded number of rows behind line l-1.  Each CTA claims B consecutive
 // lines in order (an atomic counter; lines a CTA waits for belong to running
 // CTAs) and gives each line two warps:
-//  - the producer computes, 8 rows at a time, c_i = (b_i - sum_far M_ij x_j) d_i
+//  - the producer computes, 8 rows at a time, c_i = b_i d_i - sum_far d_i M_ij x_j
 //    over the "far" entries (earlier lines, and own-line entries 32 or more
 //    rows back) from a window-major layout with coalesced loads, after one wait
 //    per window on the rows it needs;
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
         }
         if (lane < LANES && (lane % LPR) == 0 && ix < nx) {
           const int i = row0 + ix;
-          cs_line[ix] = (b[lp_vec<MIRROR>(i, M.n)] - acc) * M.dscale[i];
+          cs_line[ix] = b[lp_vec<MIRROR>(i, M.n)] * M.dscale[i] - acc;   // far values carry d_i
         }
       }
       if (UPDATE) {
@@ -557,7 +557,7 @@ namespace pmgk {
 // behind them and its per-row time grows about five-fold (measured: ~1000
 // instead of ~205 cycles a row).  Here the chain CTA (cluster rank 0) runs only
 // the chain warp; the producer CTA (rank 1, eight warps on all four
-// sub-partitions) computes c_i = (b_i - sum_far M_ij x_j) d_i and stores it
+// sub-partitions) computes c_i = b_i d_i - sum_far d_i M_ij x_j and stores it
 // straight into the chain CTA's shared memory (distributed shared memory,
 // relaxed cluster-scope stores; the value is its own ready flag, as in
 // k_lp2).  Rank 0 claims lines in order through an atomic counter (lines it
@@ -626,30 +626,21 @@ __device__ __forceinline__ double lp4_get_c(const double* p, bool need, unsigned
   if (__any_sync(0xffffffffu, need && v == kPending)) v = lp4_wait_c_uniform(p, need, v, err);
   return need ? __longlong_as_double((long long)v) : 0.0;
 }
-// Producer side: the 8 values raw[] of this lane's columns jj[] (jj < 0:
-// none), waiting while any lane of the warp has one pending.
+// Producer side: the value of column j (j < 0: none) for this lane, waiting
+// while any lane of the warp has its value pending.
 template <bool MIRROR>
-__device__ __noinline__ void lp4_wait_x_uniform(const double* x, int n, const int* jj, unsigned long long* raw,
-                                                unsigned* err) {
+__device__ __noinline__ unsigned long long lp4_wait_x1_uniform(const double* x, int n, int j, unsigned long long v,
+                                                               unsigned* err) {
   const long long t0 = clock64();
   for (unsigned it = 1;; ++it) {
     __nanosleep(it < 16 ? 20 : 100);
-    bool pend = false;
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-      if (raw[t] == kPending) {
-        raw[t] = ld_relaxed_u64(x + lp_vec<MIRROR>(jj[t], n));
-        pend |= raw[t] == kPending;
-      }
-    if (!__any_sync(0xffffffffu, pend)) return;
+    if (v == kPending) v = ld_relaxed_u64(x + lp_vec<MIRROR>(j, n));
+    if (!__any_sync(0xffffffffu, v == kPending)) return v;
     if ((it & 15u) == 0u) {
       const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
       if (__any_sync(0xffffffffu, expired)) {
         if ((threadIdx.x & 31) == 0) atomicOr(err, 1u);
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-          if (raw[t] == kPending) raw[t] = 0ull;
-        return;
+        return v == kPending ? 0ull : v;
       }
     }
   }
@@ -669,13 +660,18 @@ __device__ __noinline__ void lp4_producer(Lp2 M, const double* __restrict__ b, d
     const int o = M.wofs[W], K = (M.wofs[W + 1] - o) / LANES;
     const int ix = w * WIN + lane / LPR;
     const bool valid = lane < LANES && ix < nx;
+    const bool head = valid && (lane % LPR) == 0;
+    // b_i d_i before any wait (the far values carry d_i), so that only the
+    // reduction follows the last far value
+    const double bd = head ? b[lp_vec<MIRROR>(row0 + ix, M.n)] * M.dscale[row0 + ix] : 0.0;
     double a = 0.0;
-    // K is the same for every lane of the window: the loop and its waits stay warp-uniform
+    // K is the same for every lane of the window: the loop and its waits stay
+    // warp-uniform.  Entries are in column order, the order in which earlier
+    // lines finish them, so each entry is summed as soon as every lane has it.
     for (int k0 = 0; k0 < K; k0 += 8) {
       int jj[8];
       double vv[8];
       unsigned long long raw[8];
-      bool pend = false;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const bool in = valid && k0 + t < K;
@@ -683,21 +679,22 @@ __device__ __noinline__ void lp4_producer(Lp2 M, const double* __restrict__ b, d
         vv[t] = in ? M.wval[o + LANES * (k0 + t) + lane] : 0.0;
       }
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        raw[t] = jj[t] >= 0 ? ld_relaxed_u64(x + lp_vec<MIRROR>(jj[t], M.n)) : 0ull;
-        pend |= raw[t] == kPending;
-      }
-      if (__any_sync(0xffffffffu, pend)) lp4_wait_x_uniform<MIRROR>(x, M.n, jj, raw, err);
+      for (int t = 0; t < 8; ++t) raw[t] = jj[t] >= 0 ? ld_relaxed_u64(x + lp_vec<MIRROR>(jj[t], M.n)) : 0ull;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) a = fma(vv[t], __longlong_as_double((long long)raw[t]), a);
+      for (int t = 0; t < 8; ++t) {
+        if (k0 + t < K) {   // uniform: padding slots of the window cost nothing
+          if (__any_sync(0xffffffffu, raw[t] == kPending)) raw[t] = lp4_wait_x1_uniform<MIRROR>(x, M.n, jj[t], raw[t], err);
+          a = fma(vv[t], __longlong_as_double((long long)raw[t]), a);
+        }
+      }
     }
     if (LPR > 1) {
 #pragma unroll
       for (int off = 1; off < LPR; off <<= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
     }
-    if (lane < LANES && (lane % LPR) == 0 && ix < nx) {
+    if (head) {
       const int i = row0 + ix;
-      const double c = (b[lp_vec<MIRROR>(i, M.n)] - a) * M.dscale[i];
+      const double c = bd - a;
       // a NaN must never read as the pending marker
       const unsigned long long cb = (unsigned long long)__double_as_longlong(c) == kPending
                                         ? 0x7FF8000000000000ull : (unsigned long long)__double_as_longlong(c);

@@ -785,7 +785,7 @@ LpLayout build_lp(const Csr& M, int nx, const std::vector<double>* dinv, int win
           add_need(ln - jl, j - jl * nx);
           const int lane = lpr * r + (cnt % lpr);
           far[size_t(lane)].push_back(j);
-          farv[size_t(lane)].push_back(M.v[t]);
+          farv[size_t(lane)].push_back(M.v[t] * P.dscale[size_t(i)]);
           ++cnt;
           ++P.far_entries;
         }

@@ -29,7 +29,8 @@ struct Csr {
 //  - "far" part: all other entries, grouped in windows of `win` rows of one
 //    line with `lpr` lanes per row: lane = lpr*r + s (r: row in window), slot k
 //    of lane l is entry s + lpr*k of that row, wcol/wval[wofs[w] + win*lpr*k
-//    + l] (col -1 = padding).
+//    + l] (col -1 = padding); values scaled by d_i, so that
+//    x_i = b_i d_i - sum_far wval x_j - (ring part).
 //  - wait list of window w: pairs (line distance, rows needed) in
 //    wait[waitofs[w] .. waitofs[w+1]).
 //  - dscale[i] = d_i (1 when the matrix has a unit diagonal).
