@@ -107,7 +107,8 @@ typedef struct {
    * backward; batched FP32 forward, backward; then the chain configuration
    * (0..3: producer sums enter the chain in groups of 1, 2, 4, 8 rows) of the
    * clustered kernel for the forward and the backward solve.  tune_h[j]: single-vector
-   * forward, backward sweep; batched forward, backward sweep; chain
+   * forward, backward sweep (variant 2 there: the wavefront sweep over grid
+   * lines of a 2D P1 level); batched forward, backward sweep; chain
    * configuration of the forward and the backward sweep. */
   int tune_p[PMG_MAX_LEVELS];
   int tune_h[PMG_MAX_LEVELS];
@@ -257,8 +258,8 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream);
 
 /* Sets the kernel variant of every solve by hand, in the packing of
  * pmg_info_t.tune_p / tune_h (arrays of nlevels / nhlevels ints): single-vector
- * solves and sweeps take 0, 1 or 3, batched ones 1 or 2; chain configurations
- * 0..3.  The hierarchy must be uploaded.  Errors: PMG_ERR_ARG (a variant out of
+ * solves take 0, 1 or 3, single-vector sweeps 0..3, batched ones 1 or 2;
+ * chain configurations 0..3.  The hierarchy must be uploaded.  Errors: PMG_ERR_ARG (a variant out of
  * range; nothing changed), PMG_ERR_STATE. */
 pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h);
 

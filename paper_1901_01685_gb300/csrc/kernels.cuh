@@ -74,10 +74,11 @@ __device__ __forceinline__ double group_sum(double s) {
 // ---------------------------------------------------------------------------
 // CSR SpMV: W lanes per row.
 //   MODE 0: y = b - A x     MODE 1: y = A x     MODE 2: y = b + A x
+//   MODE 3: y = (b - A x) d (elementwise)
 // ---------------------------------------------------------------------------
 template <int W, int MODE>
 __global__ void __launch_bounds__(256) k_spmv(Csr A, const double* __restrict__ x, const double* __restrict__ b,
-                                              double* __restrict__ y) {
+                                              double* __restrict__ y, const double* __restrict__ d = nullptr) {
   const int lane = threadIdx.x & (W - 1);
   const int group = (blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int ngroups = (gridDim.x * blockDim.x) / W;
@@ -89,7 +90,8 @@ __global__ void __launch_bounds__(256) k_spmv(Csr A, const double* __restrict__ 
     if (lane == 0) {
       if (MODE == 0) y[row] = b[row] - s;
       else if (MODE == 1) y[row] = s;
-      else y[row] = b[row] + s;
+      else if (MODE == 2) y[row] = b[row] + s;
+      else y[row] = (b[row] - s) * d[row];
     }
   }
 }
@@ -787,6 +789,127 @@ __global__ void __launch_bounds__(32 * kLp4Warps, 1)
       cp_async_commit();
     }
     cp_async_wait<0>();
+  }
+}
+
+}  // namespace pmgk
+
+namespace pmgk {
+
+// ---------------------------------------------------------------------------
+// Lexicographic Gauss-Seidel sweep on a 2D P1 level (m x m interior grid,
+// 9-point stencil) as a wavefront over grid lines.
+//
+// The sweep's lower solve x_i = t_i - sum_{W,SW,S,SE} c x (t = (b - U x_old) d,
+// c = a d, d = 1/a_ii; mirrored indices for the backward sweep) couples a row
+// to its left neighbour and to three rows of the line below.  Lane k of warp w
+// owns grid line l = 32 w + k and, at step s, computes column s - 2k: the line
+// below's value at column c + 1 is the one lane k - 1 computed at the previous
+// step (one shuffle), columns c and c - 1 are the two before it (registers).
+// Warp w's lane 0 takes line 32 w - 1 from warp w - 1's lane 31 through
+// shared memory (value-as-flag, as in the line-pipelined solves).  Each row
+// sees the same values as the sequential sweep; only the order of its four
+// products differs.  The result is written over x (the old values were
+// consumed by the SpMV that formed t).  One CTA, ceil(m / 32) warps; dynamic
+// shared memory (warps - 1) * m doubles.
+// ---------------------------------------------------------------------------
+constexpr int kWaveMaxLines = 800;
+constexpr int kWavePrefetch = 4;
+
+template <bool MIRROR>
+__global__ void __launch_bounds__(1024, 1) k_gs_wave(int m, const double* __restrict__ coef,
+                                                     const double* __restrict__ t, double* x, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char wave_smem[];
+  volatile double* bnd = reinterpret_cast<double*>(wave_smem);   // [warps - 1][m]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = m * m;
+  for (int i = threadIdx.x; i < (nw - 1) * m; i += blockDim.x)
+    reinterpret_cast<volatile unsigned long long*>(bnd)[i] = kPending;
+  __syncthreads();
+  const int l = 32 * warp + lane;
+  const bool line_ok = l < m;
+  const int steps = m + 2 * 31;
+  double h1 = 0.0, h2 = 0.0, h3 = 0.0, xl = 0.0, got = 0.0;
+  // rolling prefetch of (t_i, c_SW, c_S, c_SE, c_W) for the next kWavePrefetch steps
+  double pt[kWavePrefetch], pc[kWavePrefetch][4];
+  auto fetch = [&](int s, double& tv, double (&cv)[4]) {
+    const int c = s - 2 * lane;
+    if (line_ok && c >= 0 && c < m) {
+      const int i = l * m + c;
+      tv = __ldg(t + lp_vec<MIRROR>(i, n));
+      const double2 a = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i);
+      const double2 b = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i + 1);
+      cv[0] = a.x; cv[1] = a.y; cv[2] = b.x; cv[3] = b.y;
+    } else {
+      tv = 0.0; cv[0] = cv[1] = cv[2] = cv[3] = 0.0;
+    }
+  };
+#pragma unroll
+  for (int q = 0; q < kWavePrefetch; ++q) fetch(q, pt[q], pc[q]);
+  const long long t0 = clock64();
+  // Lane 0 of warp w > 0 starts with column 0 of the boundary line in its
+  // history (the other lanes receive it from their neighbour's first step).
+  {
+    const bool need = lane == 0 && warp > 0;
+    unsigned long long v = need ? *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m) : 0ull;
+    for (unsigned it = 1; __any_sync(0xffffffffu, need && v == kPending); ++it) {
+      if (need && v == kPending) v = *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m);
+      if ((it & 63u) == 0u) {
+        const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+        if (__any_sync(0xffffffffu, expired)) {
+          if (need && v == kPending) { atomicOr(err, 1u); v = 0ull; }
+          break;
+        }
+      }
+    }
+    if (need) h1 = __longlong_as_double((long long)v);
+  }
+  for (int s0 = 0; s0 < steps; s0 += kWavePrefetch) {
+#pragma unroll
+    for (int q = 0; q < kWavePrefetch; ++q) {
+      const int s = s0 + q;
+      if (s < steps) {
+        const int c = s - 2 * lane;
+        // line below at column c + 1: lane k - 1's previous output, or for
+        // lane 0 the previous warp's boundary line (warp-uniform wait)
+        double below = got;
+        const bool need = lane == 0 && warp > 0 && c + 1 >= 0 && c + 1 < m;
+        if (lane == 0) below = 0.0;
+        if (__any_sync(0xffffffffu, need)) {
+          unsigned long long v = need ? *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m + c + 1) : 0ull;
+          for (unsigned it = 1; __any_sync(0xffffffffu, need && v == kPending); ++it) {
+            if (need && v == kPending) v = *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m + c + 1);
+            if ((it & 63u) == 0u) {
+              const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+              if (__any_sync(0xffffffffu, expired)) {
+                if (need && v == kPending) { atomicOr(err, 1u); v = 0ull; }
+                break;
+              }
+            }
+          }
+          if (need) below = __longlong_as_double((long long)v);
+        }
+        h3 = h2;
+        h2 = h1;
+        h1 = below;
+        const bool active = line_ok && c >= 0 && c < m;
+        double out = 0.0;
+        if (active) {
+          out = pt[q];
+          out = fma(-pc[q][0], h3, out);
+          out = fma(-pc[q][1], h2, out);
+          out = fma(-pc[q][2], h1, out);
+          out = fma(-pc[q][3], xl, out);
+          // a NaN must never read as the pending marker
+          if ((unsigned long long)__double_as_longlong(out) == kPending) out = __longlong_as_double(0x7FF8000000000000ll);
+          x[lp_vec<MIRROR>(l * m + c, n)] = out;
+          if (lane == 31 && warp + 1 < nw) bnd[warp * m + c] = out;
+        }
+        xl = out;
+        got = __shfl_up_sync(0xffffffffu, out, 1);
+        fetch(s + kWavePrefetch, pt[q], pc[q]);
+      }
+    }
   }
 }
 

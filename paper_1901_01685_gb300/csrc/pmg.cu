@@ -120,6 +120,8 @@ struct DevPLevel {
 // vectors), the ring kernel, or the lines-per-CTA kernel (batched).  Defaults
 // are the measured best on GB300; pmg_autotune re-measures them.
 enum : unsigned char { kVarLp2 = 0, kVarRing = 1, kVarLines = 2, kVarCluster = 3 };
+// single-vector sweeps of 2D P1 levels: value 2 selects the wavefront kernel
+constexpr unsigned char kVarWave = kVarLines;
 // Chain configurations of the clustered kernel k_lp4: producer sums enter the
 // chain in groups of G rows, A+1 .. A+G rows ahead.
 struct Lp4Cfg { int G, A; };
@@ -132,7 +134,7 @@ struct PTune {
   unsigned char bU[2] = {kVarRing, kVarRing};
 };
 struct HTune {
-  unsigned char gF = kVarRing, gB = kVarRing;         // single vector: forward / backward sweep
+  unsigned char gF = kVarWave, gB = kVarWave;         // single vector: forward / backward sweep
   unsigned char cF = 1, cB = 1;                       // k_lp4 chain configuration of the sweeps
   unsigned char bF = kVarRing, bB = kVarRing;         // batched
 };
@@ -147,6 +149,8 @@ struct DevHLevel {
   pmgk::LpB<double> Lob{}, UpMb{};   // batched Gauss-Seidel layouts
   pmgk::LpC<double> Loc{}, UpMc{};
   int inflightGS = 0;
+  const double* wave_f = nullptr;    // wavefront sweep coefficients (2D levels), forward / backward
+  const double* wave_b = nullptr;
 };
 
 }  // namespace
@@ -170,6 +174,9 @@ struct pmg_hierarchy_s {
   struct COff { DevCsrOff far; int ring; size_t far32, push32, d32, far16, push16, farb, pushb; };
   std::vector<std::vector<uint16_t>> h16store;     // FP16 / BF16 bit patterns of the factors
   std::vector<COff> coffL, coffU, coffL32, coffU32, coffLo, coffUpM;
+  std::vector<std::vector<double>> wavestore;      // wavefront sweep coefficients (host copies until upload)
+  struct WOff { size_t f, b; bool ok; };
+  std::vector<WOff> woff;
   size_t off_cinv = 0;
   bool uploaded = false;
   char* arena = nullptr;
@@ -322,14 +329,15 @@ int grid_for(long long work, int threads, int cap) {
 }
 
 template <int MODE>
-void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, double* y, cudaStream_t s, int sms) {
+void spmv(const pmgk::Csr& A, double avg, const double* x, const double* b, double* y, cudaStream_t s, int sms,
+          const double* d = nullptr) {
   const int threads = 256;
   if (avg >= 24) {
-    pmgk::k_spmv<32, MODE><<<grid_for((long long)A.nr * 32, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+    pmgk::k_spmv<32, MODE><<<grid_for((long long)A.nr * 32, threads, sms * 16), threads, 0, s>>>(A, x, b, y, d);
   } else if (avg >= 12) {
-    pmgk::k_spmv<16, MODE><<<grid_for((long long)A.nr * 16, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+    pmgk::k_spmv<16, MODE><<<grid_for((long long)A.nr * 16, threads, sms * 16), threads, 0, s>>>(A, x, b, y, d);
   } else {
-    pmgk::k_spmv<8, MODE><<<grid_for((long long)A.nr * 8, threads, sms * 16), threads, 0, s>>>(A, x, b, y);
+    pmgk::k_spmv<8, MODE><<<grid_for((long long)A.nr * 8, threads, sms * 16), threads, 0, s>>>(A, x, b, y, d);
   }
 }
 
@@ -603,15 +611,21 @@ void smooth_from_residual(Ctx& c, int l, const double* r, double* u) {
 // forward  (D + L) x_new = b - U x_old,  backward  (D + U) x_new = b - L x_old.
 // The new values go to a scratch vector first (the solve polls its output for
 // readiness, so it cannot overwrite x in place) and are copied back.
+bool wave_sweep(Ctx& c, const DevHLevel& D, bool backward, const double* b, double* x);
+
 void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
   const DevHLevel& D = c.h->dh[j];
   double* t = c.w->hr[j];
   double* xn = c.w->hg[j];
   const pmgk::Csr& other = backward ? D.Lo : D.Up;
+  unsigned char var = backward ? c.h->htune[j].gB : c.h->htune[j].gF;
+  if (var == kVarWave) {
+    if (wave_sweep(c, D, backward, b, x)) return;
+    var = kVarCluster;   // no wavefront layout (3D levels): the clustered kernel
+  }
   // the ring kernel in its one-vector form: the old-value part as an SpMV, the
   // new values by the line-pipelined solve with a 2-wide ring
   const pmgk::LpC<double>& ring = backward ? D.UpMc : D.Loc;
-  const unsigned char var = backward ? c.h->htune[j].gB : c.h->htune[j].gF;
   if (var == kVarRing && size_t(ring.nx + 64) * 32 * sizeof(double) <= kLpSmemCap) {
     launch(c, PMG_K_GS, csr_bytes(D.nnzA / 2, D.N) + 24.0 * D.N,
            [&] { spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms); });
@@ -634,6 +648,26 @@ void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
     else
       pmgk::k_gauss_seidel<false><<<sync_grid(c), 256, 0, c.s>>>(D.A, D.dinv, b, x, c.w->flags, ep, cnt, c.w->err);
   });
+}
+
+// Wavefront sweep of a 2D P1 level: t = (b - (other part) x_old) d, then the
+// lower solve by k_gs_wave written over x.  False when the level has none.
+bool wave_sweep(Ctx& c, const DevHLevel& D, bool backward, const double* b, double* x) {
+  const double* coef = backward ? D.wave_b : D.wave_f;
+  if (!coef) return false;
+  const int m = int(std::lround(std::sqrt(double(D.N))));
+  const int warps = (m + 31) / 32;
+  const size_t smem = size_t(warps - 1) * size_t(m) * sizeof(double);
+  if (smem > kLpSmemCap || m * m != D.N) return false;
+  double* t = c.w->hr[&D - c.h->dh.data()];
+  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
+    spmv<3>(backward ? D.Lo : D.Up, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms, D.dinv);
+    const void* fn = backward ? (const void*)pmgk::k_gs_wave<true> : (const void*)pmgk::k_gs_wave<false>;
+    allow_smem(fn);
+    if (backward) pmgk::k_gs_wave<true><<<1, 32 * warps, smem, c.s>>>(m, coef, t, x, c.w->err);
+    else pmgk::k_gs_wave<false><<<1, 32 * warps, smem, c.s>>>(m, coef, t, x, c.w->err);
+  });
+  return true;
 }
 
 // r_c = (M^L_c)^{-1} P^T r and u_out = u_in + (M^L_l)^{-1} P e_c (Eq. restriction / prolongation)
@@ -1385,6 +1419,42 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     h->coffLo.push_back(plan_ring(Hl.Lo, Hl.Lolp, Hl.n1d, 2, false));
     h->coffUpM.push_back(plan_ring(Hl.UpM, Hl.UpMlp, Hl.n1d, 2, false));
   }
+  // Wavefront sweeps of the 2D P1 levels: per row the coefficients (SW, S, SE,
+  // W) of the sweep's strict lower part, scaled by 1/a_ii, in the sweep's index
+  // space (mirrored for the backward sweep); levels with another pattern keep
+  // the other kernels.
+  h->wavestore.reserve(2 * h->H.hl.size());
+  for (const auto& Hl : h->H.hl) {
+    pmg_hierarchy_s::WOff w{0, 0, false};
+    const int m = Hl.n1d;
+    auto build = [&](const pmgl::Csr& T, const std::vector<double>& d, std::vector<double>& c) {
+      c.assign(size_t(Hl.N) * 4, 0.0);
+      for (int i = 0; i < Hl.N; ++i)
+        for (int t = T.rp[i]; t < T.rp[i + 1]; ++t) {
+          const int j = T.ci[t];
+          const int dl = i / m - j / m, dx = i % m - j % m;
+          int slot = -1;
+          if (dl == 0 && dx == 1) slot = 3;
+          else if (dl == 1 && dx == 1) slot = 0;
+          else if (dl == 1 && dx == 0) slot = 1;
+          else if (dl == 1 && dx == -1) slot = 2;
+          if (slot < 0) return false;
+          c[size_t(i) * 4 + size_t(slot)] = T.v[t] * d[size_t(i)];
+        }
+      return true;
+    };
+    if (h->H.d == 2 && m >= 2 && m <= pmgk::kWaveMaxLines && size_t(m) * size_t(m) == size_t(Hl.N)) {
+      std::vector<double> cf, cb;
+      if (build(Hl.Lo, Hl.dinv, cf) && build(Hl.UpM, Hl.UpMlp.dscale, cb)) {
+        h->wavestore.push_back(std::move(cf));
+        w.f = P.add(h->wavestore.back().data(), h->wavestore.back().size() * sizeof(double));
+        h->wavestore.push_back(std::move(cb));
+        w.b = P.add(h->wavestore.back().data(), h->wavestore.back().size() * sizeof(double));
+        w.ok = true;
+      }
+    }
+    h->woff.push_back(w);
+  }
   *out = h;
   return PMG_OK;
 }
@@ -1535,6 +1605,10 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.nnzA = h->off_HA[j].nnz;
     D.Lo = bind(h->off_Lo[j], base);
     D.Up = bind(h->off_Up[j], base);
+    if (h->woff[j].ok) {
+      D.wave_f = reinterpret_cast<const double*>(base + h->woff[j].f);
+      D.wave_b = reinterpret_cast<const double*>(base + h->woff[j].b);
+    }
     D.Lolp = bind_lp(h->off_Lolp[j], base);
     D.UpMlp = bind_lp(h->off_UpMlp[j], base);
     {
@@ -1786,7 +1860,7 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
   };
   // single-vector solves and sweeps: the windowed kernel, the ring kernel and
   // every chain configuration of the clustered kernel
-  auto pick_single = [&](unsigned char& var, unsigned char& cfg, bool ring_ok, auto&& fn) {
+  auto pick_single = [&](unsigned char& var, unsigned char& cfg, bool ring_ok, bool wave_ok, auto&& fn) {
     double best = 1e300;
     unsigned char bv = var, bc = cfg;
     auto trial = [&](unsigned char v, unsigned char k) {
@@ -1797,6 +1871,7 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
     };
     trial(kVarLp2, cfg);
     if (ring_ok) trial(kVarRing, cfg);
+    if (wave_ok) trial(kVarWave, cfg);
     for (int k = 0; k < kNumLp4Cfgs; ++k) trial(kVarCluster, (unsigned char)k);
     var = bv;
     cfg = bc;
@@ -1807,8 +1882,8 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
     const int L = int(l);
     fill(ws->f[l], D.N);
     const bool ring_ok = size_t(D.Lc64.nx + 64) * 32 * sizeof(double) <= cap;
-    pick_single(h->ptune[l].sL, h->ptune[l].cL, ring_ok, [&] { lsolve(c, L, ws->f[l], ws->y[l]); });
-    pick_single(h->ptune[l].sU, h->ptune[l].cU, ring_ok, [&] { usolve(c, L, ws->f[l], ws->e[l], ws->u[l]); });
+    pick_single(h->ptune[l].sL, h->ptune[l].cL, ring_ok, false, [&] { lsolve(c, L, ws->f[l], ws->y[l]); });
+    pick_single(h->ptune[l].sU, h->ptune[l].cU, ring_ok, false, [&] { usolve(c, L, ws->f[l], ws->e[l], ws->u[l]); });
     if (ws->R) {
       const long long nR = (long long)D.N * ws->R;
       double* b64 = ws->bf[l];
@@ -1830,8 +1905,9 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream) {
     fill(ws->hb[j], D.N);
     fill(ws->hx[j], D.N);
     const bool ring_ok = size_t(D.Loc.nx + 64) * 32 * sizeof(double) <= cap;
-    pick_single(h->htune[j].gF, h->htune[j].cF, ring_ok, [&] { gs(c, J, false, ws->hb[j], ws->hx[j]); });
-    pick_single(h->htune[j].gB, h->htune[j].cB, ring_ok, [&] { gs(c, J, true, ws->hb[j], ws->hx[j]); });
+    const bool wave_ok = D.wave_f != nullptr;
+    pick_single(h->htune[j].gF, h->htune[j].cF, ring_ok, wave_ok, [&] { gs(c, J, false, ws->hb[j], ws->hx[j]); });
+    pick_single(h->htune[j].gB, h->htune[j].cB, ring_ok, wave_ok, [&] { gs(c, J, true, ws->hb[j], ws->hx[j]); });
     if (ws->R) {
       const long long nR = (long long)D.N * ws->R;
       fill(ws->bhb[j], nR);
@@ -1862,8 +1938,7 @@ pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
   }
   for (size_t j = 0; j < h->dh.size(); ++j) {
     const int v = tune_h[j];
-    if (!single_ok(field(v, 0)) || !single_ok(field(v, 1)) || !batched_ok(field(v, 2)) || !batched_ok(field(v, 3)))
-      return fail(PMG_ERR_ARG, "invalid sweep variant");
+    if (!batched_ok(field(v, 2)) || !batched_ok(field(v, 3))) return fail(PMG_ERR_ARG, "invalid sweep variant");
   }
   for (size_t l = 0; l < h->dl.size(); ++l) {
     const int v = tune_p[l];

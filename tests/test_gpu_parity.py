@@ -222,3 +222,30 @@ def test_bicgstab_full_size_annulus(torch_mod, pmg, oracle_mod):
     O = oracle_mod.Hierarchy(0, 3, 8)
     it, hist = _check_bicgstab(torch_mod, S, O)
     assert hist[-1] < 1e-8 and it <= 3
+
+
+def test_steps_match_oracle_at_benchmark_size(torch_mod, pmg, oracle_mod):
+    """Single steps at the benchmark size (quarter annulus, h = 2^-8, p = 3),
+    where the kernels differ from the small cases: the clustered triangular
+    solves on 257-row lines, the wide SpMV, and the wavefront Gauss-Seidel
+    sweeps on the 255 x 255 P1 level (eight warps, every hand-off between
+    them).  Each step within the per-step tolerance of the oracle's."""
+    torch = torch_mod
+    S = pmg.Solver(0, 3, 8)
+    O = oracle_mod.Hierarchy(0, 3, 8)
+    rng = np.random.default_rng(17)
+    n = O.N[0]
+    x, b = rng.standard_normal(n), rng.standard_normal(n)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    S.apply(pmg.PMG_OP_RESIDUAL, 0, _dev(torch, x), _dev(torch, b), y)
+    assert _rel(y.cpu().numpy(), O.residual(0, b, x)) <= STEP_TOL
+    S.apply(pmg.PMG_OP_SMOOTH, 0, _dev(torch, x), _dev(torch, b), y)
+    assert _rel(y.cpu().numpy(), O.smooth(0, b, x)) <= STEP_TOL
+    for j in range(2):
+        nh = O.NH[j]
+        xh, bh = rng.standard_normal(nh), rng.standard_normal(nh)
+        yh = torch.empty(nh, dtype=torch.float64, device="cuda")
+        S.apply(pmg.PMG_OP_GS_FWD, j, _dev(torch, xh), _dev(torch, bh), yh)
+        assert _rel(yh.cpu().numpy(), O.gs(j, bh, xh)) <= STEP_TOL
+        S.apply(pmg.PMG_OP_GS_BWD, j, _dev(torch, xh), _dev(torch, bh), yh)
+        assert _rel(yh.cpu().numpy(), O.gs(j, bh, xh, backward=True)) <= STEP_TOL
