@@ -78,6 +78,7 @@ def lib():
         L.or_ilut.argtypes = [C.c_int, ip, ip, dp, C.c_double, C.c_double, ip, ip,
                               ip, ip, dp, ip, ip, dp, C.c_int]
         L.or_ilut_budget.argtypes = [C.c_longlong, C.c_int, C.c_double]
+        L.or_use_consistent.argtypes = [C.c_void_p]
         L.or_full_matrix.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip, ip, ip, dp]
         L.or_full_load.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp]
         _lib = L
@@ -193,13 +194,18 @@ class Hierarchy:
 
     def __init__(self, domain: int, p: int, k: int, tau: float = 1e-12, fill: float = 1.0,
                  projection: int = INDIRECT, exact: int = U_SINPROD, nu1: int = 1, nu2: int = 1,
-                 coarse_cycles: int = 2):
+                 coarse_cycles: int = 2, consistent: bool = False):
         st = C.c_int()
         self._L = lib()
         self._h = self._L.or_setup(domain, p, k, tau, fill, projection, exact, nu1, nu2,
                                    coarse_cycles, C.byref(st))
         if not self._h:
             raise RuntimeError(f"or_setup failed: {STATUS.get(st.value, st.value)}")
+        # transfers with the consistent mass matrices instead of the lumped ones (App. B)
+        if consistent:
+            cst = self._L.or_use_consistent(self._h)
+            if cst:
+                raise RuntimeError(f"or_use_consistent failed: {STATUS.get(cst, cst)}")
         self.domain, self.p, self.k, self.projection = domain, p, k, projection
         self.nlev = self._L.or_nlev(self._h)
         self.nh = self._L.or_nh(self._h)

@@ -684,6 +684,7 @@ typedef struct {
   double* ML;          /* lumped mass, interior */
   csr P;               /* P_{coarse}^{q}: N_q x N_coarse (interior, unscaled) */
   csr Pt;              /* its transpose */
+  double* MCB; int mcb;   /* consistent transfers: banded Cholesky factor of the interior mass, half bandwidth */
 } plevel;
 
 typedef struct {
@@ -698,6 +699,8 @@ typedef struct or_hier {
   int nlev;
   plevel lev[16];
   double* ML1;         /* lumped mass of V_{h,1}, interior */
+  int consistent;      /* 1: transfers with the consistent mass matrices (App. B) */
+  double* MC1B; int mc1b;   /* banded Cholesky factor of the interior mass of V_{h,1} */
   int nh;
   hlevel hl[16];
   double* LUc; int* piv; int Nc;
@@ -705,13 +708,13 @@ typedef struct or_hier {
   double* uB;          /* full-space boundary coefficients (degree p) */
 } or_hier;
 
-static void lev_free(plevel* l) { csr_free(&l->A); csr_free(&l->L); csr_free(&l->U); csr_free(&l->P); csr_free(&l->Pt); free(l->ML); }
+static void lev_free(plevel* l) { csr_free(&l->A); csr_free(&l->L); csr_free(&l->U); csr_free(&l->P); csr_free(&l->Pt); free(l->ML); free(l->MCB); }
 
 void or_free(or_hier* h) {
   if (!h) return;
   for (int l = 0; l < h->nlev; ++l) lev_free(&h->lev[l]);
   for (int j = 0; j < h->nh; ++j) { csr_free(&h->hl[j].A); csr_free(&h->hl[j].P); csr_free(&h->hl[j].R); }
-  free(h->ML1); free(h->LUc); free(h->piv); free(h->f); free(h->uB);
+  free(h->ML1); free(h->MC1B); free(h->LUc); free(h->piv); free(h->f); free(h->uB);
   free(h);
 }
 
@@ -936,18 +939,73 @@ static void coarse_solve(const or_hier* h, const double* r1, double* e1) {
 static int coarse_N(const or_hier* h, int l) { return (l + 1 < h->nlev) ? h->lev[l + 1].N : h->hl[0].N; }
 static const double* coarse_ML(const or_hier* h, int l) { return (l + 1 < h->nlev) ? h->lev[l + 1].ML : h->ML1; }
 
-/* restriction I_q^{qc}: r_c = (M^L_{qc})^{-1} P_q^{qc} r  (Eq. restriction, lumped) */
+/* Banded Cholesky M = L L^T of a symmetric positive definite CSR matrix: row i
+ * of L holds L_ij, j = i-b..i, at B[i*(b+1) + (i-j)]; *b: half bandwidth. */
+static int band_cholesky(const csr* M, int* bout, double** Bout) {
+  int n = M->nr, b = 0;
+  for (int i = 0; i < n; ++i)
+    for (int t = M->rp[i]; t < M->rp[i + 1]; ++t) if (i - M->ci[t] > b) b = i - M->ci[t];
+  double* B = calloc((size_t)n * (size_t)(b + 1), sizeof(double));
+  if (!B) return OR_ERR_OOM;
+  for (int i = 0; i < n; ++i)
+    for (int t = M->rp[i]; t < M->rp[i + 1]; ++t) {
+      int j = M->ci[t];
+      if (j <= i) B[(size_t)i * (b + 1) + (i - j)] = M->v[t];
+    }
+  for (int i = 0; i < n; ++i) {
+    int j0 = i - b > 0 ? i - b : 0;
+    for (int j = j0; j <= i; ++j) {
+      double s = B[(size_t)i * (b + 1) + (i - j)];
+      int k0 = (i - b > j - b ? i - b : j - b); if (k0 < 0) k0 = 0;
+      for (int k = k0; k < j; ++k) s -= B[(size_t)i * (b + 1) + (i - k)] * B[(size_t)j * (b + 1) + (j - k)];
+      if (j == i) {
+        if (!(s > 0.0)) { free(B); return OR_ERR_ZERO_PIVOT; }
+        B[(size_t)i * (b + 1)] = sqrt(s);
+      } else {
+        B[(size_t)i * (b + 1) + (i - j)] = s / B[(size_t)j * (b + 1)];
+      }
+    }
+  }
+  *bout = b; *Bout = B;
+  return OR_OK;
+}
+/* y <- M^{-1} y with the factor of band_cholesky: L z = y, then L^T y = z */
+static void band_solve(int n, int b, const double* B, double* y) {
+  for (int i = 0; i < n; ++i) {
+    double s = y[i];
+    for (int j = (i - b > 0 ? i - b : 0); j < i; ++j) s -= B[(size_t)i * (b + 1) + (i - j)] * y[j];
+    y[i] = s / B[(size_t)i * (b + 1)];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k <= i + b && k < n; ++k) s -= B[(size_t)k * (b + 1) + (k - i)] * y[k];
+    y[i] = s / B[(size_t)i * (b + 1)];
+  }
+}
+
+/* restriction I_q^{qc}: r_c = (M_{qc})^{-1} P_q^{qc} r  (Eq. restriction), with
+ * the lumped mass M^L (default) or the consistent mass M (App. B) */
 static void restrict_(const or_hier* h, int l, const double* r, double* rc) {
   spmv(&h->lev[l].Pt, r, rc);
+  if (h->consistent) {
+    if (l + 1 < h->nlev) band_solve(h->lev[l + 1].N, h->lev[l + 1].mcb, h->lev[l + 1].MCB, rc);
+    else band_solve(h->hl[0].N, h->mc1b, h->MC1B, rc);
+    return;
+  }
   const double* ml = coarse_ML(h, l);
   for (int i = 0; i < coarse_N(h, l); ++i) rc[i] /= ml[i];
 }
-/* prolongation I_{qc}^{q}: u += (M^L_q)^{-1} P_{qc}^{q} e_c  (Eq. prolongation, lumped) */
+/* prolongation I_{qc}^{q}: u += (M_q)^{-1} P_{qc}^{q} e_c  (Eq. prolongation), lumped or consistent */
 static void prolong_add(const or_hier* h, int l, const double* ec, double* u) {
   const plevel* L = &h->lev[l];
   double* t = dalloc(L->N);
   spmv(&L->P, ec, t);
-  for (int i = 0; i < L->N; ++i) u[i] += t[i] / L->ML[i];
+  if (h->consistent) {
+    band_solve(L->N, L->mcb, L->MCB, t);
+    for (int i = 0; i < L->N; ++i) u[i] += t[i];
+  } else {
+    for (int i = 0; i < L->N; ++i) u[i] += t[i] / L->ML[i];
+  }
   free(t);
 }
 
@@ -1035,6 +1093,29 @@ int or_get_ml(const or_hier* h, int l, double* out) {
   if (l == h->nlev) { memcpy(out, h->ML1, sizeof(double) * (size_t)h->hl[0].N); return OR_OK; }
   return OR_ERR_ARG;
 }
+/* Switches the hierarchy's transfers to the consistent mass matrices (App. B):
+ * assembles the interior mass matrix of every degree level and of V_{h,1}
+ * (the quadrature of the lumped ones) and factors each by banded Cholesky. */
+int or_use_consistent(or_hier* h) {
+  int ne = 1 << h->k, st;
+  for (int l = 0; l <= h->nlev; ++l) {
+    int q = l < h->nlev ? h->lev[l].q : 1;
+    slotmat m;
+    csr M;
+    st = assemble(h->dom, h->d, ne, q, q, K_MASS, 0, h->ex, &m);
+    if (st) return st;
+    st = slots_to_csr(&m, 1, &M);
+    slot_free(&m);
+    if (st) { csr_free(&M); return st; }
+    if (l < h->nlev) st = band_cholesky(&M, &h->lev[l].mcb, &h->lev[l].MCB);
+    else st = band_cholesky(&M, &h->mc1b, &h->MC1B);
+    csr_free(&M);
+    if (st) return st;
+  }
+  h->consistent = 1;
+  return OR_OK;
+}
+
 int or_get_rhs(const or_hier* h, double* f) { memcpy(f, h->f, sizeof(double) * (size_t)h->lev[0].N); return OR_OK; }
 
 /* step-level entry points (one hot-path row each) */

@@ -92,8 +92,10 @@ def test_batched_fp64_matches_oracle_per_rhs(torch_mod, pmg, oracle_mod, case):
 
 
 # extra cycles allowed over the FP64 oracle: FP32 perturbs the preconditioner
-# by ~1e-7 relative, FP16 / BF16 factor storage by ~5e-4 / ~4e-3 relative
-EXTRA_CYCLES = {1: 2, 2: 3, 3: 6}
+# by ~1e-7 relative, FP16 / BF16 factor storage by ~5e-4 / ~4e-3 relative; the
+# perturbed V-cycle still contracts by well under 0.1 a cycle (Table 2a), so
+# one (FP32) or two (16-bit factors) extra cycles cover it
+EXTRA_CYCLES = {1: 1, 2: 2, 3: 2}
 
 
 @pytest.mark.parametrize("case", CASES)

@@ -656,3 +656,69 @@ def test_cdr_table4_and_table5_counts(oracle_mod):
         assert st == "ok" and abs(it - vc[6][p - 2]) <= 2, (p, it, hist)
         _, hist, it, st = h.bicgstab(f, u0)
         assert st == "ok" and abs(it - bi[6][p - 2]) <= 1, (p, it, hist)
+
+
+# --------------------------------------------------------------------------
+# Consistent-mass transfers (App. B): the oracle's option
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dom", [0, 1])
+def test_consistent_transfers_reproduce_shared_functions(oracle_mod, dom):
+    """With the consistent mass, prolongation and restriction between degree
+    levels q >= 3 and q - 1 >= 2 are L2 projections onto the target space, so
+    a function of both spaces that vanishes on the boundary (here
+    xi (1 - xi) eta (1 - eta), degree 2 per direction; its boundary
+    coefficients are zero) maps to itself exactly, in any measure (the
+    annulus weights the projection by |det J|).  The interior-only solve of
+    the oracle is exact for it because the function's boundary coefficients
+    vanish."""
+    O = oracle_mod
+    k, p = 4, 4
+    ne = 1 << k
+    H = O.Hierarchy(dom, p, k, consistent=True)
+    g = lambda s: s * (1.0 - s)
+    for lev in range(H.nlev - 1):           # transfers q -> q - 1 with q - 1 >= 2
+        q, qc = p - lev, p - lev - 1
+        cq = np.kron(_interp_interior(q, ne, g), _interp_interior(q, ne, g))
+        cc = np.kron(_interp_interior(qc, ne, g), _interp_interior(qc, ne, g))
+        up = H.prolong_add(lev, cc, np.zeros(H.N[lev]))
+        assert np.abs(up - cq).max() <= 1e-11 * np.abs(cq).max(), (lev, np.abs(up - cq).max())
+        rc = H.restrict(lev, cq)
+        assert np.abs(rc - cc).max() <= 1e-11 * np.abs(cc).max(), (lev, np.abs(rc - cc).max())
+
+
+@pytest.mark.parametrize("dom", [0, 1])
+def test_consistent_transfers_to_p1_converge_at_second_order(oracle_mod, dom):
+    """Between degree 2 and the P1 space (no shared function vanishing on the
+    boundary), the consistent L2 projections of a smooth function's
+    interpolant converge at the P1 rate 2 over the whole domain (no lumping
+    error at the boundary)."""
+    O = oracle_mod
+    g1d = lambda s: np.sin(np.pi * s)
+    errs_p, errs_r = [], []
+    for k in (4, 5, 6, 7):
+        ne = 1 << k
+        H = O.Hierarchy(dom, 2, k, consistent=True)
+        c2 = np.kron(_interp_interior(2, ne, g1d), _interp_interior(2, ne, g1d))
+        c1 = np.kron(_interp_interior(1, ne, g1d), _interp_interior(1, ne, g1d))
+        errs_p.append(_l2_param_error(2, ne, H.prolong_add(0, c1, np.zeros(H.N[0])), g1d, 0.0, 1.0))
+        errs_r.append(_l2_param_error(1, ne, H.restrict(0, c2), g1d, 0.0, 1.0))
+    for errs in (errs_p, errs_r):
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+        assert min(rates) > 2 - 0.2, (errs_p, errs_r)
+
+
+def test_appB_consistent_counts(oracle_mod):
+    """Soft pin against App. B's consistent-mass V-cycle counts (ILUT,
+    benchmark 1, direct projection) within +-2, as for Table 4."""
+    O = oracle_mod
+    from paper_1901_01685_gb300 import inputs
+    rows = [list(map(int, l.split())) for l in open(os.path.join(GOLDEN, "appB_consistent_vcycles.txt"))
+            if l.strip() and not l.startswith("#")]
+    for row in rows:
+        k = row[0]
+        if k > 7:
+            continue
+        for p, paper in zip((2, 3, 4, 5), row[1:]):
+            H = O.Hierarchy(O.ANNULUS, p, k, projection=O.DIRECT, exact=O.U_PAPER_B1, consistent=True)
+            it = H.solve(H.rhs(), inputs.initial_guess(H.N[0], 1))[2]
+            assert abs(it - paper) <= 2, (k, p, it, paper)
