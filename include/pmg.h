@@ -76,8 +76,16 @@ typedef struct {
   int projection;     /* pmg_projection; default PMG_PROJ_INDIRECT */
   int coarse_cycles;  /* h-multigrid V-cycles per coarse solve; default 2 (Sec. 3) */
   int exact;          /* pmg_exact; default PMG_U_SINPROD */
-  int reserved;       /* must be 0 */
+  int transfer_mass;  /* mass matrix of the L2-projection transfers (Sec. 3, App. B):
+                         PMG_MASS_LUMPED (default, the paper's choice) or
+                         PMG_MASS_CONSISTENT (single-vector solves only) */
 } pmg_options;
+
+/* Transfer mass matrix (Sec. 3 "Prolongation and restriction", App. B):
+ * lumped (row sums, a diagonal) or consistent (solved exactly through its
+ * tensor-product structure: one banded Cholesky solve per grid line and
+ * direction). */
+enum { PMG_MASS_LUMPED = 0, PMG_MASS_CONSISTENT = 1 };
 
 #define PMG_MAX_LEVELS 16
 
@@ -147,7 +155,8 @@ pmg_status pmg_workspace_bytes(pmg_handle h, int max_rhs, size_t* bytes);
 
 /* Creates a workspace in caller-owned device memory `mem_dev` (>= the size from
  * pmg_workspace_bytes, 256-byte aligned); initialises it on `stream`.
- * *out is owned by the caller (pmg_ws_destroy). */
+ * *out is owned by the caller (pmg_ws_destroy).  PMG_ERR_ARG for max_rhs > 1
+ * on a hierarchy set up with PMG_MASS_CONSISTENT transfers. */
 pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem_dev, size_t bytes,
                                 void* stream, pmg_ws* out);
 

@@ -914,3 +914,138 @@ __global__ void __launch_bounds__(1024, 1) k_gs_wave(int m, const double* __rest
 }
 
 }  // namespace pmgk
+
+namespace pmgk {
+
+// ---------------------------------------------------------------------------
+// Sliced-ELL SpMV (residual and transfer operators).  Rows in slices of 32,
+// one row per lane; each slice holds its widest row's entry count rounded up
+// to a multiple of 4, in groups of four entries a row: per group the column
+// indices (one int4 a lane, 512 B a warp), the values of entries 0, 1 (one
+// double2 a lane) and of entries 2, 3 (one double2 a lane), each block
+// lane-major, so every load is a coalesced 16-byte-per-lane access and every
+// lane runs its own FMA chain (no reductions).  Padding slots have column -1
+// and are skipped.
+//   MODE 0: y = b - A x   1: y = A x   2: y = b + A x   3: y = (b - A x) d
+// One warp per slice (8 per CTA), at most 32 registers a thread so that 64
+// warps fit an SM: the SM's FP64 pipe is near its limit at 2 flop per 12
+// bytes, and the resident warps hide the gathers (measured 0.63 of the HBM
+// copy rate cold at 81 non-zeros a row, against 0.51 with 48 warps an SM).
+// ---------------------------------------------------------------------------
+struct Sell {
+  int nr, nslices;
+  const long long* sofs;   // [nslices + 1] first slot of each slice (multiple of 128)
+  const int4* col4;        // [slots / 4]
+  const double2* val2;     // [slots / 2]
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 8) k_sell(Sell S, const double* __restrict__ x, const double* __restrict__ b,
+                                              double* __restrict__ y, const double* __restrict__ d) {
+  const int lane = threadIdx.x & 31;
+  const int slice = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (slice >= S.nslices) return;
+  const long long base = __ldg(S.sofs + slice), end = __ldg(S.sofs + slice + 1);
+  const int groups = int((end - base) >> 7);            // groups of 4 entries (128 slots)
+  const int4* c4 = S.col4 + (base >> 2) + lane;          // 32 int4 a group
+  const double2* v2 = S.val2 + (base >> 1) + lane;       // 64 double2 a group: entries 0,1 then 2,3
+  double acc = 0.0;
+#pragma unroll 2
+  for (int g = 0; g < groups; ++g) {
+    const int4 c = __ldg(c4 + 32 * g);
+    const double2 va = __ldg(v2 + 64 * g);
+    const double2 vb = __ldg(v2 + 64 * g + 32);
+    const double x0 = c.x >= 0 ? __ldg(x + c.x) : 0.0;
+    const double x1 = c.y >= 0 ? __ldg(x + c.y) : 0.0;
+    const double x2 = c.z >= 0 ? __ldg(x + c.z) : 0.0;
+    const double x3 = c.w >= 0 ? __ldg(x + c.w) : 0.0;
+    acc = fma(va.x, x0, acc);
+    acc = fma(va.y, x1, acc);
+    acc = fma(vb.x, x2, acc);
+    acc = fma(vb.y, x3, acc);
+  }
+  const int row = slice * 32 + lane;
+  if (row < S.nr) {
+    if (MODE == 0) y[row] = b[row] - acc;
+    else if (MODE == 1) y[row] = acc;
+    else if (MODE == 2) y[row] = b[row] + acc;
+    else y[row] = (b[row] - acc) * d[row];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Consistent-mass transfers (Sec. 3, App. B): y <- M_1^{-1} y along one grid
+// direction, M_1 = L L^T the banded Cholesky factor of a 1D interior mass
+// matrix of degree Q (half bandwidth Q), F[i*(Q+1)] = 1/L_ii and
+// F[i*(Q+1) + k] = L_{i,i-k} (0 where i < k).  The interior mass matrix of a
+// level is the Kronecker product of such matrices, so one pass per direction
+// inverts it.  One thread a line of n entries: line t starts at
+// (t / inner) * outer + t % inner and steps by stride.  Forward substitution
+// writes z back into y, backward substitution writes y, or out = add + y
+// when add is given (the prolongation's update).  Loads are issued eight
+// entries ahead of the dependent chain; the factor rows are broadcasts.
+// ---------------------------------------------------------------------------
+template <int Q>
+__global__ void __launch_bounds__(64) k_band_lines(int n, int nlines, long long inner, long long outer, long long stride,
+                                                   const double* __restrict__ F, double* y,
+                                                   const double* add, double* out) {
+  constexpr int kB = 8;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nlines) return;
+  double* yl = y + (t / inner) * outer + (t % inner);
+  double h[Q];
+#pragma unroll
+  for (int k = 0; k < Q; ++k) h[k] = 0.0;
+  // L z = y: z_i = (y_i - sum_k L_{i,i-k} z_{i-k}) / L_ii, h[k-1] = z_{i-k}
+  for (int i0 = 0; i0 < n; i0 += kB) {
+    double v[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) v[j] = (i0 + j < n) ? yl[(i0 + j) * stride] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const int i = i0 + j;
+      if (i < n) {
+        const double* f = F + (size_t)i * (Q + 1);
+        double s = v[j];
+#pragma unroll
+        for (int k = Q; k >= 1; --k) s = fma(-__ldg(f + k), h[k - 1], s);
+        const double z = s * __ldg(f);
+#pragma unroll
+        for (int k = Q - 1; k >= 1; --k) h[k] = h[k - 1];
+        h[0] = z;
+        yl[i * stride] = z;
+      }
+    }
+  }
+  // L^T x = z: x_i = (z_i - sum_k L_{i+k,i} x_{i+k}) / L_ii, h[k-1] = x_{i+k}
+#pragma unroll
+  for (int k = 0; k < Q; ++k) h[k] = 0.0;
+  const long long ofs = yl - y;
+  for (int i0 = n - 1; i0 >= 0; i0 -= kB) {
+    double v[kB], a[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const int i = i0 - j;
+      v[j] = i >= 0 ? yl[i * stride] : 0.0;
+      a[j] = (add && i >= 0) ? add[ofs + i * stride] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const int i = i0 - j;
+      if (i >= 0) {
+        double s = v[j];
+#pragma unroll
+        for (int k = Q; k >= 1; --k)
+          if (i + k < n) s = fma(-__ldg(F + (size_t)(i + k) * (Q + 1) + k), h[k - 1], s);
+        const double x = s * __ldg(F + (size_t)i * (Q + 1));
+#pragma unroll
+        for (int k = Q - 1; k >= 1; --k) h[k] = h[k - 1];
+        h[0] = x;
+        if (add) out[ofs + i * stride] = a[j] + x;
+        else yl[i * stride] = x;
+      }
+    }
+  }
+}
+
+}  // namespace pmgk

@@ -59,6 +59,44 @@ struct Packer {
 
 struct DevCsrOff { int nr; long long nnz; size_t rp, ci, v; };
 
+// Sliced-ELL copy of a CSR matrix (k_sell): host arrays, kept until upload.
+struct SellHost {
+  int nr = 0, nslices = 0;
+  std::vector<long long> sofs;
+  std::vector<int> col;
+  std::vector<double> val;
+};
+SellHost make_sell(const pmgl::Csr& a) {
+  SellHost S;
+  S.nr = a.nr;
+  S.nslices = (a.nr + 31) / 32;
+  S.sofs.assign(size_t(S.nslices) + 1, 0);
+  for (int s = 0; s < S.nslices; ++s) {
+    int w = 0;
+    for (int r = s * 32; r < std::min(a.nr, s * 32 + 32); ++r) w = std::max(w, a.rp[r + 1] - a.rp[r]);
+    w = (w + 3) / 4 * 4;
+    S.sofs[size_t(s) + 1] = S.sofs[size_t(s)] + 32LL * w;
+  }
+  S.col.assign(size_t(S.sofs.back()), -1);
+  S.val.assign(size_t(S.sofs.back()), 0.0);
+  for (int s = 0; s < S.nslices; ++s) {
+    const long long base = S.sofs[size_t(s)];
+    for (int lane = 0; lane < 32; ++lane) {
+      const int r = s * 32 + lane;
+      if (r >= a.nr) continue;
+      for (int k = a.rp[r]; k < a.rp[r + 1]; ++k) {
+        const int e = k - a.rp[r], g = e / 4, t = e % 4;
+        const long long grp = base + 128LL * g;
+        S.col[size_t(grp + 4 * lane + t)] = a.ci[k];
+        // values: entries 0, 1 of every lane, then entries 2, 3 of every lane
+        S.val[size_t(grp + (t < 2 ? 0 : 64) + 2 * lane + (t & 1))] = a.v[k];
+      }
+    }
+  }
+  return S;
+}
+struct SellOff { int nr, nslices; size_t sofs, col, val; };
+
 DevCsrOff plan_csr(Packer& P, const pmgl::Csr& a) {
   DevCsrOff o;
   o.nr = a.nr;
@@ -99,11 +137,20 @@ pmgk::Lp2 bind_lp(const LpOff& o, char* base) {
 
 constexpr size_t kLpSmemCap = 200 * 1024;
 
+// Consistent-mass transfers: banded Cholesky factors of the 1D interior mass
+// matrices of a level (first direction, the others), n interior functions a
+// direction, degree q.  f0 == nullptr: lumped transfers.
+struct MassF {
+  const double* f0 = nullptr;
+  const double* f1 = nullptr;
+  int n = 0, q = 0;
+};
 struct DevPLevel {
   int N = 0;
   double avg_nnz = 0;
   long long nnzA = 0, nnzL = 0, nnzU = 0, nnzP = 0;
   pmgk::Csr A{}, L{}, U{}, Pro{}, Res{};
+  pmgk::Sell sA{}, sPro{}, sRes{};   // sliced-ELL copies for the residual and the transfers
   const double* udinv = nullptr;
   pmgk::Lp2 Llp{}, Ulp{};         // line-pipelined layouts (U mirrored)
   // batched solves: FP32 copies for the inner cycle, plain CSR layouts
@@ -115,6 +162,7 @@ struct DevPLevel {
   pmgk::LpC<float, __half> Lc16{}, Uc16{};           // FP16 / BF16 factor storage, FP32 arithmetic
   pmgk::LpC<float, __nv_bfloat16> Lcb{}, Ucb{};
   int inflightL = 0, inflightU = 0;    // lines of one group the solve's pipeline keeps busy at once
+  MassF mass{};                        // consistent transfers: factors of this level's mass matrix
 };
 // Kernel variant of each solve: the line-pipelined windowed kernel (single
 // vectors), the ring kernel, or the lines-per-CTA kernel (batched).  Defaults
@@ -175,9 +223,14 @@ struct pmg_hierarchy_s {
   std::vector<std::vector<uint16_t>> h16store;     // FP16 / BF16 bit patterns of the factors
   std::vector<COff> coffL, coffU, coffL32, coffU32, coffLo, coffUpM;
   std::vector<std::vector<double>> wavestore;      // wavefront sweep coefficients (host copies until upload)
+  std::vector<SellHost> sellstore;                  // sliced-ELL copies of A, P, R per level (host, until upload)
+  std::vector<SellOff> soffA, soffPro, soffRes;
   struct WOff { size_t f, b; bool ok; };
   std::vector<WOff> woff;
   size_t off_cinv = 0;
+  struct MOff { size_t f0, f1; int n, q; };
+  std::vector<MOff> moff;             // consistent transfers: per p-level, then V_{h,1}
+  MassF mass1{};                      // factors of V_{h,1}'s mass matrix (consistent transfers)
   bool uploaded = false;
   char* arena = nullptr;
   std::vector<DevPLevel> dl;
@@ -380,9 +433,9 @@ cudaEvent_t pool_event(pmg_ws w) {
 // Issues one kernel launch (the callable), counting it and, when profiling is
 // on, bracketing it with CUDA events on the launch stream.
 template <class F>
-void launch(Ctx& c, int cls, double bytes, F&& f) {
+void launch(Ctx& c, int cls, double bytes, F&& f, int kernels = 1) {
   pmg_ws w = c.w;
-  ++w->launches;
+  w->launches += kernels;
   if (!w->prof) { f(); return; }
   cudaEvent_t a = pool_event(w), b = pool_event(w);
   if (!a || !b) { f(); return; }
@@ -428,10 +481,16 @@ unsigned next_epoch(Ctx& c) {
 }
 int sync_grid(const Ctx& c) { return c.h->sms * 4; }
 
+template <int MODE>
+void sell_spmv(const pmgk::Sell& S, const double* x, const double* b, double* y, cudaStream_t s) {
+  const int threads = 256;
+  const int grid = std::max(1, (S.nslices * 32 + threads - 1) / threads);
+  pmgk::k_sell<MODE><<<grid, threads, 0, s>>>(S, x, b, y, nullptr);
+}
+
 void residual(Ctx& c, int l, const double* f, const double* u, double* r) {
   const DevPLevel& D = c.h->dl[l];
-  launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 24.0 * D.N,
-         [&] { spmv<0>(D.A, D.avg_nnz, u, f, r, c.s, c.h->sms); });
+  launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 24.0 * D.N, [&] { sell_spmv<0>(D.sA, u, f, r, c.s); });
 }
 
 // Line-pipelined solve launch (kLpLinesPerCta lines per CTA, two warps per line).
@@ -633,14 +692,19 @@ void gs(Ctx& c, int j, bool backward, const double* b, double* x) {
     cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
     return;
   }
-  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
-    spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms);
-    const pmgk::Lp2& lay = backward ? D.UpMlp : D.Lolp;
-    const int cfg = backward ? c.h->htune[j].cB : c.h->htune[j].cF;
-    if ((var == kVarCluster && lp4_launch(c, cfg, lay, backward, t, xn, nullptr)) || lp_launch(c, lay, backward, t, xn, nullptr)) {
-      cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
-      return;
-    }
+  const pmgk::Lp2& lay = backward ? D.UpMlp : D.Lolp;
+  const int cfg = backward ? c.h->htune[j].cB : c.h->htune[j].cF;
+  const double half = csr_bytes(D.nnzA / 2, D.N);
+  launch(c, PMG_K_GS, half + 24.0 * D.N, [&] { spmv<0>(other, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms); });
+  bool done = false;
+  launch(c, PMG_K_GS, half + 16.0 * D.N, [&] {
+    done = (var == kVarCluster && lp4_launch(c, cfg, lay, backward, t, xn, nullptr)) || lp_launch(c, lay, backward, t, xn, nullptr);
+  });
+  if (done) {
+    cudaMemcpyAsync(x, xn, size_t(D.N) * sizeof(double), cudaMemcpyDeviceToDevice, c.s);
+    return;
+  }
+  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 16.0 * D.N, [&] {
     const unsigned ep = next_epoch(c);
     unsigned* cnt = next_counter(c);
     if (backward)
@@ -660,8 +724,11 @@ bool wave_sweep(Ctx& c, const DevHLevel& D, bool backward, const double* b, doub
   const size_t smem = size_t(warps - 1) * size_t(m) * sizeof(double);
   if (smem > kLpSmemCap || m * m != D.N) return false;
   double* t = c.w->hr[&D - c.h->dh.data()];
-  launch(c, PMG_K_GS, csr_bytes(D.nnzA, D.N) + 48.0 * D.N, [&] {
+  const double nnz_old = 0.5 * double(D.nnzA - D.N);   // strictly lower / upper part (symmetric pattern)
+  launch(c, PMG_K_GS, 12.0 * nnz_old + 4.0 * (D.N + 1) + 32.0 * D.N, [&] {
     spmv<3>(backward ? D.Lo : D.Up, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms, D.dinv);
+  });
+  launch(c, PMG_K_GS, 48.0 * D.N, [&] {
     const void* fn = backward ? (const void*)pmgk::k_gs_wave<true> : (const void*)pmgk::k_gs_wave<false>;
     allow_smem(fn);
     if (backward) pmgk::k_gs_wave<true><<<1, 32 * warps, smem, c.s>>>(m, coef, t, x, c.w->err);
@@ -670,16 +737,58 @@ bool wave_sweep(Ctx& c, const DevHLevel& D, bool backward, const double* b, doub
   return true;
 }
 
-// r_c = (M^L_c)^{-1} P^T r and u_out = u_in + (M^L_l)^{-1} P e_c (Eq. restriction / prolongation)
+// y <- M^{-1} y for a level's interior mass matrix M (consistent transfers):
+// one banded line solve per direction; with add, the last pass writes
+// out = add + M^{-1} y instead of y.
+void mass_solve(Ctx& c, const MassF& m, double* y, const double* add, double* out) {
+  const int d = c.h->H.d;
+  long long total = 1;
+  for (int k = 0; k < d; ++k) total *= m.n;
+  const int nlines = int(total / m.n);
+  long long inner = 1;
+  for (int dir = 0; dir < d; ++dir) {
+    const bool last = dir == d - 1;
+    const double* F = dir == 0 ? m.f0 : m.f1;
+    const double* a = last ? add : nullptr;
+    double* o = last ? out : nullptr;
+    launch(c, PMG_K_TRANSFER, 16.0 * double(total) + (a ? 16.0 * double(total) : 0.0), [&] {
+      const int grid = (nlines + 63) / 64;
+      switch (m.q) {
+#define PMG_BAND_CASE(Q) \
+  case Q: pmgk::k_band_lines<Q><<<grid, 64, 0, c.s>>>(m.n, nlines, inner, inner * m.n, inner, F, y, a, o); break;
+        PMG_BAND_CASE(1) PMG_BAND_CASE(2) PMG_BAND_CASE(3) PMG_BAND_CASE(4)
+        PMG_BAND_CASE(5) PMG_BAND_CASE(6) PMG_BAND_CASE(7) PMG_BAND_CASE(8)
+#undef PMG_BAND_CASE
+        default: c.w->note(cudaErrorInvalidValue, "mass_solve: degree out of range");
+      }
+    });
+    inner *= m.n;
+  }
+}
+
+// r_c = M_c^{-1} P^T r and u_out = u_in + M_l^{-1} P e_c (Eq. restriction /
+// prolongation), M the lumped mass matrices (folded into the operators) or
+// the consistent ones (App. B; the operators are then the unscaled P, P^T)
 void restrict_to(Ctx& c, int l, const double* r, double* rc) {
   const DevPLevel& D = c.h->dl[l];
   launch(c, PMG_K_TRANSFER, csr_bytes(D.nnzP, D.Res.nr) + 8.0 * (D.N + D.Res.nr),
-         [&] { spmv<1>(D.Res, double(D.nnzP) / std::max(1, D.Res.nr), r, nullptr, rc, c.s, c.h->sms); });
+         [&] { sell_spmv<1>(D.sRes, r, nullptr, rc, c.s); });
+  if (D.mass.f0) {
+    const bool last = l + 1 == int(c.h->dl.size());
+    mass_solve(c, last ? c.h->mass1 : c.h->dl[l + 1].mass, rc, nullptr, nullptr);
+  }
 }
 void prolong_add(Ctx& c, int l, const double* ec, const double* uin, double* uout) {
   const DevPLevel& D = c.h->dl[l];
+  if (D.mass.f0) {
+    double* t = c.w->y[l];
+    launch(c, PMG_K_TRANSFER, csr_bytes(D.nnzP, D.N) + 8.0 * (D.N + D.Res.nr),
+           [&] { sell_spmv<1>(D.sPro, ec, nullptr, t, c.s); });
+    mass_solve(c, D.mass, t, uin, uout);
+    return;
+  }
   launch(c, PMG_K_TRANSFER, csr_bytes(D.nnzP, D.N) + 8.0 * (2 * D.N + D.Res.nr),
-         [&] { spmv<2>(D.Pro, double(D.nnzP) / std::max(1, D.N), ec, uin, uout, c.s, c.h->sms); });
+         [&] { sell_spmv<2>(D.sPro, ec, uin, uout, c.s); });
 }
 
 // one h-multigrid V-cycle on P1 level j: A_j x = b (Sec. 3, Fig. 1)
@@ -810,7 +919,7 @@ pmg_status krylov_dot(Ctx& c, const double* x, const double* y, double* out) {
   launch(c, PMG_K_NORM, 16.0 * N, [&] {
     pmgk::k_dot_partial<<<pmgk::kNormBlocks, pmgk::kNormThreads, 0, c.s>>>(N, x, y, c.w->partial);
     pmgk::k_sum_partials<<<1, pmgk::kNormThreads, 0, c.s>>>(pmgk::kNormBlocks, c.w->partial, c.w->kd);
-  });
+  }, 2);
   PMG_CUDA(cudaMemcpyAsync(out, c.w->kd, sizeof(double), cudaMemcpyDeviceToHost, c.s));
   return finish_launches(c);
 }
@@ -833,8 +942,7 @@ pmg_status bicgstab_impl(pmg_handle h, pmg_ws ws, const double* f, const double*
     launch(c, PMG_K_NORM, 24.0 * N, [&] { pmgk::k_sub_scaled<<<gb, 256, 0, c.s>>>(N, x, a, y, out); });
   };
   auto matvec = [&](const double* x, double* y) {
-    launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 16.0 * D.N,
-           [&] { spmv<1>(D.A, D.avg_nnz, x, nullptr, y, c.s, h->sms); });
+    launch(c, PMG_K_RESIDUAL, csr_bytes(D.nnzA, D.N) + 16.0 * D.N, [&] { sell_spmv<1>(D.sA, x, nullptr, y, c.s); });
   };
   if (iters) *iters = 0;
   pmg_status st = begin_launches(c);
@@ -1119,7 +1227,7 @@ pmg_status slots_load_impl(Ctx& c, int slot0, int n, const double* F, const doub
     pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
     pmgk::k_slots_start<<<1, 128, 0, c.s>>>(pmgk::kNormBlocks, R, slot0, n, ws->bpart, ws->br0, ws->brel,
                                             ws->bmask, ws->bstate, ws->biters);
-  });
+  }, 2);
   for (int k = slot0; k < slot0 + n; ++k) ws->slot_state[k] = 1;
   PMG_CUDA(cudaGetLastError());
   return PMG_OK;
@@ -1152,7 +1260,7 @@ pmg_status slots_cycle_body(Ctx& c, int precision, double tol) {
     pmgk::k_sqnorm_partial_b<<<pmgk::kNormBlocks, 128, 0, c.s>>>(N, R, ws->bR, ws->bpart);
     pmgk::k_slots_update<<<(R + 127) / 128, 128, 0, c.s>>>(pmgk::kNormBlocks, R, tol, ws->bpart, ws->br0, ws->brel,
                                                            ws->bmask, ws->bstate, ws->biters);
-  });
+  }, 2);
   PMG_CUDA(cudaMemcpyAsync(ws->hm.relres, ws->brel, R * sizeof(double), cudaMemcpyDeviceToHost, c.s));
   PMG_CUDA(cudaMemcpyAsync(ws->hm.state, ws->bstate, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
   PMG_CUDA(cudaMemcpyAsync(ws->hm.iters, ws->biters, R * sizeof(int), cudaMemcpyDeviceToHost, c.s));
@@ -1308,7 +1416,7 @@ pmg_status pmg_default_options(pmg_options* opt) {
   opt->projection = PMG_PROJ_INDIRECT;
   opt->coarse_cycles = 2;
   opt->exact = PMG_U_SINPROD;
-  opt->reserved = 0;
+  opt->transfer_mass = PMG_MASS_LUMPED;
   return PMG_OK;
 }
 
@@ -1317,7 +1425,8 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
   *out = nullptr;
   pmg_options o;
   if (opt) o = *opt; else pmg_default_options(&o);
-  if (o.reserved != 0) return fail(PMG_ERR_ARG, "options.reserved must be 0");
+  if (o.transfer_mass != PMG_MASS_LUMPED && o.transfer_mass != PMG_MASS_CONSISTENT)
+    return fail(PMG_ERR_ARG, "options.transfer_mass must be PMG_MASS_LUMPED or PMG_MASS_CONSISTENT");
   pmg_hierarchy_s* h = nullptr;
   try {
     h = new pmg_hierarchy_s();
@@ -1337,6 +1446,15 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     h->off_U.push_back(plan_csr(P, L.U));
     h->off_Pro.push_back(plan_csr(P, L.Pro));
     h->off_Res.push_back(plan_csr(P, L.Res));
+    auto plan_sell = [&](const pmgl::Csr& a) {
+      h->sellstore.push_back(make_sell(a));
+      const SellHost& S = h->sellstore.back();
+      return SellOff{S.nr, S.nslices, P.add(S.sofs.data(), S.sofs.size() * sizeof(long long)),
+                     P.add(S.col.data(), S.col.size() * sizeof(int)), P.add(S.val.data(), S.val.size() * sizeof(double))};
+    };
+    h->soffA.push_back(plan_sell(L.A));
+    h->soffPro.push_back(plan_sell(L.Pro));
+    h->soffRes.push_back(plan_sell(L.Res));
     auto& ud = h->udinv_host[l];
     ud.resize(L.udiag.size());
     for (size_t i = 0; i < ud.size(); ++i) ud[i] = 1.0 / L.udiag[i];
@@ -1353,6 +1471,15 @@ pmg_status pmg_setup(int domain, int p, int log2_inv_h, const pmg_options* opt, 
     h->off_UpMlp.push_back(plan_lp(P, Hl.UpMlp));
   }
   h->off_cinv = P.add(h->H.coarse_inv.data(), h->H.coarse_inv.size() * sizeof(double));
+  if (o.transfer_mass == PMG_MASS_CONSISTENT) {
+    const int ne = 1 << log2_inv_h;
+    auto plan_mass = [&](const std::vector<double>& f0, const std::vector<double>& f1, int q) {
+      return pmg_hierarchy_s::MOff{P.add(f0.data(), f0.size() * sizeof(double)), P.add(f1.data(), f1.size() * sizeof(double)),
+                                   ne + q - 2, q};
+    };
+    for (const auto& L : h->H.lev) h->moff.push_back(plan_mass(L.MF0, L.MF1, L.q));
+    h->moff.push_back(plan_mass(h->H.M1F0, h->H.M1F1, 1));
+  }
   // FP32 copies (inner cycle of the mixed-precision batched solve) and CSR
   // layouts of the mirrored factors for the batched line-pipelined solve
   auto f32 = [&](const std::vector<double>& v) {
@@ -1549,6 +1676,13 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     D.U = bind(h->off_U[l], base);
     D.Pro = bind(h->off_Pro[l], base);
     D.Res = bind(h->off_Res[l], base);
+    auto bind_sell = [&](const SellOff& o) {
+      return pmgk::Sell{o.nr, o.nslices, reinterpret_cast<const long long*>(base + o.sofs),
+                        reinterpret_cast<const int4*>(base + o.col), reinterpret_cast<const double2*>(base + o.val)};
+    };
+    D.sA = bind_sell(h->soffA[l]);
+    D.sPro = bind_sell(h->soffPro[l]);
+    D.sRes = bind_sell(h->soffRes[l]);
     D.udinv = reinterpret_cast<const double*>(base + h->off_udinv[l]);
     D.nnzA = h->off_A[l].nnz;
     D.nnzL = h->off_L[l].nnz;
@@ -1629,6 +1763,13 @@ pmg_status pmg_upload(pmg_handle h, void* arena, size_t bytes, void* stream) {
     h->dh.push_back(D);
   }
   h->cinv = reinterpret_cast<const double*>(base + h->off_cinv);
+  if (!h->moff.empty()) {
+    auto bind_mass = [&](const pmg_hierarchy_s::MOff& m) {
+      return MassF{reinterpret_cast<const double*>(base + m.f0), reinterpret_cast<const double*>(base + m.f1), m.n, m.q};
+    };
+    for (size_t l = 0; l < h->dl.size(); ++l) h->dl[l].mass = bind_mass(h->moff[l]);
+    h->mass1 = bind_mass(h->moff.back());
+  }
   h->ptune.assign(h->dl.size(), PTune{});
   h->htune.assign(h->dh.size(), HTune{});
   h->uploaded = true;
@@ -1650,6 +1791,8 @@ pmg_status pmg_workspace_bytes(pmg_handle h, int max_rhs, size_t* bytes) {
 pmg_status pmg_workspace_create(pmg_handle h, int max_rhs, void* mem, size_t bytes, void* stream, pmg_ws* out) {
   if (!h || !mem || !out || max_rhs < 1) return fail(PMG_ERR_ARG, "invalid argument");
   *out = nullptr;
+  if (max_rhs > 1 && h->H.opt.transfer_mass == PMG_MASS_CONSISTENT)
+    return fail(PMG_ERR_ARG, "consistent-mass transfers support single-vector solves only (max_rhs must be 1)");
   WsLayout W = plan_ws(h, max_rhs);
   if (bytes < W.total) return fail(PMG_ERR_ARG, "workspace memory too small");
   if (reinterpret_cast<uintptr_t>(mem) % kAlign) return fail(PMG_ERR_ARG, "workspace memory not 256-byte aligned");

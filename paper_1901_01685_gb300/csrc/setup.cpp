@@ -408,6 +408,47 @@ void interior_csr(const SlotMatrix& S, Csr& out) {
   }
 }
 
+// Banded Cholesky factor of the interior 1D mass matrix of degree q on ne
+// elements (q + 1 Gauss points an element, as for the level's operators),
+// weighted by (1 + xi) when `weighted`, times `scale`.  The interior mass
+// matrix of a level is the Kronecker product of such matrices (the quarter
+// annulus' |det J| = (pi/2)(1 + xi) separates, the quadrature is a tensor
+// rule), so its inverse is one banded solve per grid line and direction.
+// F[i*(q+1)] = 1/L_ii, F[i*(q+1) + k] = L_{i,i-k} (0 where i - k < 0).
+std::vector<double> mass_1d_factor(int ne, int q, bool weighted, double scale) {
+  const int n = ne + q, ni = n - 2, ng = q + 1, w = q + 1;
+  double gx[16], gw[16];
+  gauss_rule(ng, gx, gw);
+  Tables1D T;
+  T.build(q, ne, ng, gx);
+  std::vector<double> M(size_t(std::max(ni, 0)) * w, 0.0);   // M[i][k] = m(i, i - k), interior indices
+  for (int e = 0; e < ne; ++e)
+    for (int g = 0; g < ng; ++g) {
+      const double x = (double(e) + gx[g]) / double(ne);
+      const double wt = gw[g] / double(ne) * (weighted ? 1.0 + x : 1.0) * scale;
+      const double* B = T.val(e, g);
+      for (int a = 0; a <= q; ++a)
+        for (int b = 0; b <= a; ++b) {
+          const int i = e + a - 1, j = e + b - 1;      // interior indices (full index - 1)
+          if (i < 0 || j < 0 || i >= ni || j >= ni) continue;
+          M[size_t(i) * w + size_t(i - j)] += wt * B[a] * B[b];
+        }
+    }
+  std::vector<double> F(M.size(), 0.0);
+  for (int i = 0; i < ni; ++i) {
+    for (int k = std::min(q, i); k >= 1; --k) {        // L_{i,j}, j = i - k, in increasing j
+      const int j = i - k;
+      double s = M[size_t(i) * w + size_t(k)];
+      for (int l = std::max(0, i - q); l < j; ++l) s -= F[size_t(i) * w + size_t(i - l)] * F[size_t(j) * w + size_t(j - l)];
+      F[size_t(i) * w + size_t(k)] = s * F[size_t(j) * w];   // times 1/L_jj
+    }
+    double s = M[size_t(i) * w];
+    for (int l = std::max(0, i - q); l < i; ++l) s -= F[size_t(i) * w + size_t(i - l)] * F[size_t(i) * w + size_t(i - l)];
+    F[size_t(i) * w] = 1.0 / std::sqrt(s);
+  }
+  return F;
+}
+
 // ∫ Phi_i dOmega for the interior functions of degree q (= lumped mass row sums).
 std::vector<double> lumped_mass(int dom, int d, int ne, int q) {
   const int n = ne + q, ng = q + 1;
@@ -951,8 +992,23 @@ pmg_status build_hierarchy(int dom, int p, int k, const pmg_options& opt, Hierar
       assemble(dom, d, ne, L.q, qc, kMass, false, opt.exact, S);
       interior_csr(S, L.Praw);
       const std::vector<double>& MLc = (l + 1 < nlev) ? H.lev[size_t(l + 1)].ML : H.ML1;
-      L.Pro = scale_rows(L.Praw, L.ML);
-      L.Res = scale_rows(transpose(L.Praw), MLc);
+      if (opt.transfer_mass == PMG_MASS_CONSISTENT) {   // M^{-1} applied by line solves after the product
+        L.Pro = L.Praw;
+        L.Res = transpose(L.Praw);
+      } else {
+        L.Pro = scale_rows(L.Praw, L.ML);
+        L.Res = scale_rows(transpose(L.Praw), MLc);
+      }
+    }
+    if (opt.transfer_mass == PMG_MASS_CONSISTENT) {
+      const bool ann = dom == PMG_QUARTER_ANNULUS;
+      const double pi = 3.14159265358979323846;
+      for (auto& L : H.lev) {
+        L.MF0 = mass_1d_factor(ne, L.q, ann, ann ? 0.5 * pi : 1.0);
+        L.MF1 = ann ? mass_1d_factor(ne, L.q, false, 1.0) : L.MF0;
+      }
+      H.M1F0 = mass_1d_factor(ne, 1, ann, ann ? 0.5 * pi : 1.0);
+      H.M1F1 = ann ? mass_1d_factor(ne, 1, false, 1.0) : H.M1F0;
     }
     H.t_transfer += ms_since(t0);
     t0 = clk::now();

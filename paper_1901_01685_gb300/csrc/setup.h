@@ -60,6 +60,10 @@ struct PLevel {
   Csr Pro;                      // (M^L_q)^{-1} P_{qc}^{q}: prolongation, N_q x N_c
   Csr Res;                      // (M^L_qc)^{-1} (P_{qc}^{q})^T: restriction, N_c x N_q
   Csr Praw;                     // P_{qc}^{q} unscaled (exported for checks)
+  // consistent transfers: banded Cholesky factors of the 1D interior mass
+  // matrices (first direction, weighted by |det J| on the annulus; the
+  // others), [i][k], k = 0..q: 1/L_ii, then L_{i,i-k}
+  std::vector<double> MF0, MF1;
   int depthL = 0, depthU = 0;   // critical-path length (levels) of the two solves
   // line-pipelined solve layout: lines are runs of n1d consecutive rows
   std::vector<int> Lsplit;      // per row of L: first entry in the row's own line
@@ -85,6 +89,7 @@ struct Hierarchy {
   pmg_options opt{};
   std::vector<PLevel> lev;      // lev[0] has degree p
   std::vector<double> ML1;      // lumped mass of V_{h,1}
+  std::vector<double> M1F0, M1F1;   // consistent transfers: factors of V_{h,1}'s 1D mass matrices
   std::vector<HLevel> hl;       // hl[0]: P1 at h; last: coarsest (direct solve)
   std::vector<double> coarse_inv;   // dense inverse of the coarsest operator
   std::vector<double> f;        // interior load with Dirichlet lift

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "oom", 3: "zero_pivot", 4: "diverged", 5: 
 PMG_QUARTER_ANNULUS, PMG_UNIT_SQUARE, PMG_UNIT_CUBE, PMG_CDR_SQUARE = 0, 1, 2, 3
 PMG_U_SINPROD, PMG_U_PAPER_B1 = 0, 1
 PMG_PROJ_INDIRECT, PMG_PROJ_DIRECT = 0, 1
+PMG_MASS_LUMPED, PMG_MASS_CONSISTENT = 0, 1   # transfer mass matrix (Sec. 3, App. B)
 (PMG_OP_RESIDUAL, PMG_OP_SMOOTH, PMG_OP_LSOLVE, PMG_OP_USOLVE, PMG_OP_RESTRICT, PMG_OP_PROLONG_ADD,
  PMG_OP_COARSE_SOLVE, PMG_OP_VCYCLE, PMG_OP_GS_FWD, PMG_OP_GS_BWD, PMG_OP_HMG_VCYCLE) = range(11)
 PMG_MAX_LEVELS = 16
@@ -43,7 +44,7 @@ KERNEL_CLASSES = ("residual", "transfer", "lsolve", "usolve", "gauss_seidel", "p
 class pmg_options(C.Structure):
     _fields_ = [("drop_tol", C.c_double), ("fill_factor", C.c_double), ("nu_pre", C.c_int),
                 ("nu_post", C.c_int), ("projection", C.c_int), ("coarse_cycles", C.c_int),
-                ("exact", C.c_int), ("reserved", C.c_int)]
+                ("exact", C.c_int), ("transfer_mass", C.c_int)]
 
 
 _L16 = C.c_int * PMG_MAX_LEVELS
@@ -369,13 +370,14 @@ class Solver:
     def __init__(self, domain: int, p: int, log2_inv_h: int, projection: int = PMG_PROJ_INDIRECT,
                  exact: int = PMG_U_SINPROD, drop_tol: float = 1e-12, fill_factor: float = 1.0,
                  nu_pre: int = 1, nu_post: int = 1, coarse_cycles: int = 2, device: str = "cuda",
-                 upload: bool = True, max_rhs: int = 1, handle=None):
+                 upload: bool = True, max_rhs: int = 1, handle=None, transfer_mass: int = 0):
         if handle is not None:
             self.h = handle            # adopt a hierarchy set up elsewhere (pmg_setup)
         else:
             opt = pmg_default_options()
             opt.projection, opt.exact, opt.drop_tol, opt.fill_factor = projection, exact, drop_tol, fill_factor
             opt.nu_pre, opt.nu_post, opt.coarse_cycles = nu_pre, nu_post, coarse_cycles
+            opt.transfer_mass = transfer_mass
             self.h = pmg_setup(domain, p, log2_inv_h, opt)
         self.info = pmg_info(self.h).as_dict()
         self.N = self.info["n"][0]

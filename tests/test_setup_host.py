@@ -33,6 +33,15 @@ def test_default_options_match_paper(pmg):
     assert o.drop_tol == 1e-12 and o.fill_factor == 1.0          # Sec. 3 "Smoother"
     assert o.nu_pre == 1 and o.nu_post == 1                      # Sec. 5
     assert o.coarse_cycles == 2                                   # Sec. 3
+    assert o.transfer_mass == pmg.PMG_MASS_LUMPED                 # Sec. 3: lumped mass in the transfers
+
+
+def test_setup_rejects_unknown_transfer_mass(pmg):
+    o = pmg.pmg_default_options()
+    o.transfer_mass = 2
+    with pytest.raises(pmg.PmgError) as e:
+        pmg.pmg_setup(0, 3, 5, o)
+    assert e.value.status == pmg.PMG_ERR_ARG
 
 
 @pytest.mark.parametrize("bad", [(0, 1, 5), (0, 9, 5), (0, 3, 2), (2, 2, 7), (5, 3, 5)])
