@@ -112,12 +112,16 @@ typedef struct {
   /* kernel variant of each solve (0 windowed line-pipelined, 1 ring, 2 lines
    * per CTA, 3 chain and producers on a two-CTA cluster), two bits each.
    * tune_p[l]: single-vector forward, backward; batched FP64 forward,
-   * backward; batched FP32 forward, backward; then the chain configuration
-   * (0..3: producer sums enter the chain in groups of 1, 2, 4, 8 rows) of the
-   * clustered kernel for the forward and the backward solve.  tune_h[j]: single-vector
-   * forward, backward sweep (variant 2 there: the wavefront sweep over grid
-   * lines of a 2D P1 level); batched forward, backward sweep; chain
-   * configuration of the forward and the backward sweep. */
+   * backward; batched FP32 forward, backward (2 bits each, bits 0-11); then
+   * the chain configuration of the clustered kernel for the forward and the
+   * backward solve (3 bits each, bits 12-14 and 15-17; 0..7: producer sums
+   * enter the chain in groups of 1, 2, 4, 8 rows one line per cluster, then
+   * groups of 2 / 4 rows with two lines per cluster, 2 / 4 rows with four
+   * lines per cluster).  tune_h[j]: single-vector forward, backward sweep
+   * (variant 2 there: the wavefront sweep over grid lines of a 2D P1 level);
+   * batched forward, backward sweep (2 bits each, bits 0-7); chain
+   * configuration of the forward and the backward sweep (3 bits each, bits
+   * 8-10 and 11-13). */
   int tune_p[PMG_MAX_LEVELS];
   int tune_h[PMG_MAX_LEVELS];
 } pmg_info_t;
@@ -268,7 +272,7 @@ pmg_status pmg_autotune(pmg_handle h, pmg_ws ws, void* stream);
 /* Sets the kernel variant of every solve by hand, in the packing of
  * pmg_info_t.tune_p / tune_h (arrays of nlevels / nhlevels ints): single-vector
  * solves take 0, 1 or 3, single-vector sweeps 0..3, batched ones 1 or 2;
- * chain configurations 0..3.  The hierarchy must be uploaded.  Errors: PMG_ERR_ARG (a variant out of
+ * chain configurations 0..7.  The hierarchy must be uploaded.  Errors: PMG_ERR_ARG (a variant out of
  * range; nothing changed), PMG_ERR_STATE. */
 pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h);
 

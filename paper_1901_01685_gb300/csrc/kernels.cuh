@@ -338,6 +338,17 @@ constexpr int kLpProducers = 6;    // producer warps per line (windows dealt rou
 // in one aligned 64-bit access and no fences or counters are needed.
 constexpr unsigned long long kPending = 0xFFFFFFFFFFFFFFFFull;
 
+// v where c holds, +0.0 elsewhere, by masking the bit pattern (integer ops).
+__device__ __forceinline__ double keep_if(bool c, double v) {
+  return __longlong_as_double(__double_as_longlong(v) & (c ? -1ll : 0ll));
+}
+// the bit pattern of v, with a NaN that reads as the pending marker replaced
+// by the canonical NaN
+__device__ __forceinline__ unsigned long long publish_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b == kPending ? 0x7FF8000000000000ull : b;
+}
+
 struct Lp2 {
   int n, nx, nlines, nwin, lpr, win;
   const int* wofs;
@@ -356,6 +367,16 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const double* p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+// generic address (global memory, or this CTA's shared memory written by
+// another CTA of the cluster)
+__device__ __forceinline__ unsigned long long ld_relaxed_generic_u64(const double* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(double* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ void st_relaxed_f64(double* p, double v) {
   asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(32 * (kLpProducers + 1) * kLpLinesPerCta)
           const int s = ix & 31;
           const double coef = pc[q * 32 + ((lane - s - 1) & 31)];
           const double xi = __shfl_sync(0xffffffffu, acc, s);
-          acc = (lane == s) ? 0.0 : fma(-coef, xi, acc);
+          acc = keep_if(lane != s, fma(-coef, xi, acc));
           const int ia = ix + kLpAhead;
           if (ia < nx && lane == (ia & 31)) acc += lp_get_shared<false>(cs_line + ia, err);
           if (lane == 0) {
@@ -550,23 +571,25 @@ namespace pmgk {
 
 // ---------------------------------------------------------------------------
 // Line-pipelined lower-triangular solve with the chain and its producers on
-// different SMs: thread-block clusters of two CTAs per line.
+// different SMs: thread-block clusters of two CTAs per line, one to four
+// consecutive lines per cluster.
 //
 // Same operation and layout as k_lp2 (Lp2).  On GB300 the FP64 unit is
 // shared by a whole SM: one warp's FP64 instruction has a 64-cycle latency and
 // the SM retires about one warp-wide FP64 instruction every 19 cycles.  While
 // producer warps on the chain's SM issue their FP64 FMAs, the chain's FMA waits
 // behind them and its per-row time grows about five-fold (measured: ~1000
-// instead of ~205 cycles a row).  Here the chain CTA (cluster rank 0) runs only
-// the chain warp; the producer CTA (rank 1, eight warps on all four
+// instead of ~205 cycles a row).  Here the chain CTA (cluster rank 2k for the
+// group's line k) runs only the chain warp; the producer CTA (rank 2k + 1, eight warps on all four
 // sub-partitions) computes c_i = b_i d_i - sum_far d_i M_ij x_j and stores it
 // straight into the chain CTA's shared memory (distributed shared memory,
 // relaxed cluster-scope stores; the value is its own ready flag, as in
-// k_lp2).  Rank 0 claims lines in order through an atomic counter (lines it
-// waits for belong to running clusters) and hands the line number to rank 1;
-// one cluster barrier per line orders rank 0's reset of its c buffer before
-// rank 1's first store for the new line.  Finished values go to global memory
-// only; producers read every far value, own line included, from there.
+// k_lp2).  Rank 0 claims groups of lines in order through an atomic counter
+// (lines a cluster waits for belong to running clusters) and hands the group
+// number to the other ranks; one cluster barrier per group orders the resets
+// of the receiving buffers before the first stores for the new group.
+// Finished values go to global memory; producers read every far value from
+// there, except the previous line's when it belongs to the same cluster.
 // ---------------------------------------------------------------------------
 constexpr int kLp4Warps = 8;
 constexpr int kLp4Producers = 8;
@@ -626,37 +649,20 @@ __device__ __noinline__ unsigned long long lp4_wait_c_uniform(const double* p, b
 __device__ __forceinline__ double lp4_get_c(const double* p, bool need, unsigned* err) {
   unsigned long long v = need ? ld_cluster_local_u64(p) : 0ull;
   if (__any_sync(0xffffffffu, need && v == kPending)) v = lp4_wait_c_uniform(p, need, v, err);
-  return need ? __longlong_as_double((long long)v) : 0.0;
+  return __longlong_as_double((long long)v);   // 0 for lanes without need (never loaded)
 }
-// Producer side: the value of column j (j < 0: none) for this lane, waiting
-// while any lane of the warp has its value pending.
-template <bool MIRROR>
-__device__ __noinline__ unsigned long long lp4_wait_x1_uniform(const double* x, int n, int j, unsigned long long v,
-                                                               unsigned* err) {
-  const long long t0 = clock64();
-  for (unsigned it = 1;; ++it) {
-    __nanosleep(it < 16 ? 20 : 100);
-    if (v == kPending) v = ld_relaxed_u64(x + lp_vec<MIRROR>(j, n));
-    if (!__any_sync(0xffffffffu, v == kPending)) return v;
-    if ((it & 15u) == 0u) {
-      const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
-      if (__any_sync(0xffffffffu, expired)) {
-        if ((threadIdx.x & 31) == 0) atomicOr(err, 1u);
-        return v == kPending ? 0ull : v;
-      }
-    }
-  }
-}
-
-// Producer warp of k_lp4 (rank 1): windows role, role + kLp4Producers, ... of
-// the line; c goes to the chain CTA's buffer at cluster address cs_remote;
-// then (UPDATE) u += x for the line's rows.
+// Producer warp of k_lp4: windows role, role + kLp4Producers, ... of the
+// line; c goes to the chain CTA's buffer at cluster address cs_remote; then
+// (UPDATE) u += x for the line's rows.  xin (or nullptr): this CTA's copy of
+// the previous line, pushed row by row by that line's chain in the same
+// cluster; entries in the previous line are read there, all others from x.
 template <bool MIRROR, bool UPDATE, int WIN, int LPR>
 __device__ __noinline__ void lp4_producer(Lp2 M, const double* __restrict__ b, double* x, double* u,
-                                          unsigned cs_remote, int line, int role, int lane, unsigned* err) {
+                                          unsigned cs_remote, const double* xin, int line, int role, int lane,
+                                          unsigned* err) {
   static_assert(WIN * LPR <= 32, "window does not fit a warp");
   constexpr int LANES = WIN * LPR;
-  const int nx = M.nx, row0 = line * nx;
+  const int nx = M.nx, row0 = line * nx, prev0 = row0 - nx;
   for (int w = role; w < M.nwin; w += kLp4Producers) {
     const int W = line * M.nwin + w;
     const int o = M.wofs[W], K = (M.wofs[W + 1] - o) / LANES;
@@ -680,13 +686,39 @@ __device__ __noinline__ void lp4_producer(Lp2 M, const double* __restrict__ b, d
         jj[t] = in ? M.wcol[o + LANES * (k0 + t) + lane] : -1;
         vv[t] = in ? M.wval[o + LANES * (k0 + t) + lane] : 0.0;
       }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) raw[t] = jj[t] >= 0 ? ld_relaxed_u64(x + lp_vec<MIRROR>(jj[t], M.n)) : 0ull;
+      const double* src[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        if (k0 + t < K) {   // uniform: padding slots of the window cost nothing
-          if (__any_sync(0xffffffffu, raw[t] == kPending)) raw[t] = lp4_wait_x1_uniform<MIRROR>(x, M.n, jj[t], raw[t], err);
-          a = fma(vv[t], __longlong_as_double((long long)raw[t]), a);
+        const int j = jj[t] < 0 ? 0 : jj[t];
+        src[t] = (xin != nullptr && j >= prev0 && j < row0) ? xin + (j - prev0) : x + lp_vec<MIRROR>(j, M.n);
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) raw[t] = jj[t] >= 0 ? ld_relaxed_generic_u64(src[t]) : 0ull;
+      // Sum the entries in order as they arrive; while any is pending, re-read
+      // every pending entry of the block at once, so that one round trip to L2
+      // picks up all the rows the chain has published meanwhile (entry-by-entry
+      // polling paid one round trip per entry).  `next` and kn are warp-uniform.
+      const int kn = min(8, K - k0);   // padding slots of the window cost nothing
+      int next = 0;
+      const long long t0 = clock64();
+      for (unsigned it = 0;; ++it) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t == next && t < kn && !__any_sync(0xffffffffu, raw[t] == kPending)) {
+            a = fma(vv[t], __longlong_as_double((long long)raw[t]), a);
+            ++next;
+          }
+        if (next >= kn) break;
+        if (it >= 16) __nanosleep(32);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t >= next && raw[t] == kPending) raw[t] = ld_relaxed_generic_u64(src[t]);
+        if ((it & 15u) == 15u) {
+          const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+          if (__any_sync(0xffffffffu, expired)) {
+            if (lane == 0) atomicOr(err, 1u);
+            break;   // the remaining entries stay unsummed: the result is invalid and flagged
+          }
         }
       }
     }
@@ -712,44 +744,69 @@ __device__ __noinline__ void lp4_producer(Lp2 M, const double* __restrict__ b, d
   }
 }
 
-// Launch: grid = 2 x clusters, cluster dimension 2, 32 * kLp4Warps threads,
-// dynamic shared memory (nx rounded up to even + 3 * kLpStage * 32) doubles.
-template <bool MIRROR, bool UPDATE, int WIN, int LPR, int G, int A>
+// Launch: grid = 2 NL x clusters, cluster dimension 2 NL, 32 * kLp4Warps
+// threads, dynamic shared memory lp4_smem_doubles(nx) doubles.  A cluster
+// takes NL consecutive lines at a time (rank 2k: chain of line k, rank 2k+1:
+// its producers); line k's chain also pushes every finished value into the
+// shared memory of line k+1's producer CTA, so that the hop from a line to
+// the next inside a cluster is a distributed-shared-memory store and a local
+// poll instead of a round trip through L2.  The receiving buffer alternates
+// between two halves from one group of lines to the next: a chain may still
+// be storing its last values when the next line's producer, done with its
+// own rows, loops back and resets a buffer (the cluster barrier of the next
+// group orders those stores before the reset of the same half).
+__host__ __device__ constexpr int lp4_smem_doubles_for(int nx) {
+  return ((nx + 1) & ~1) + 3 * kLpStage * 32 > 2 * ((nx + 1) & ~1) ? ((nx + 1) & ~1) + 3 * kLpStage * 32
+                                                                   : 2 * ((nx + 1) & ~1);
+}
+template <bool MIRROR, bool UPDATE, int WIN, int LPR, int G, int A, int NL>
 __global__ void __launch_bounds__(32 * kLp4Warps, 1)
     k_lp4(Lp2 M, const double* __restrict__ b, double* x, double* u, unsigned* counter, unsigned* err) {
   static_assert(A + G < 32, "c must enter a lane after the lane was recycled");
   static_assert(kLpStage % G == 0, "groups of G rows must tile a stage");
+  static_assert(NL >= 1 && 2 * NL <= 8, "a cluster holds at most 8 CTAs");
   extern __shared__ __align__(16) unsigned char lp4_smem[];
-  __shared__ int s_line;
-  const int nx = M.nx;
+  __shared__ int s_group;
+  const int nx = M.nx, nxe = (nx + 1) & ~1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned rank = cluster_ctarank();
-  double* cs = reinterpret_cast<double*>(lp4_smem);   // rank 0: [nx] producer sums c_i
-  double* pbuf = cs + ((nx + 1) & ~1);                  // rank 0: [3][kLpStage][32] push coefficients
-                                                        // (16-byte aligned: cp.async destinations)
-  const unsigned cs_remote = dsmem_addr(cs, 0);         // rank 1 stores into rank 0's c buffer
-  const unsigned line_remote = dsmem_addr(&s_line, 1);
-  cluster_barrier();   // both CTAs running before any distributed shared memory access
-  for (;;) {
-    __syncthreads();     // rank 0: the chain is done with the previous line's c buffer
-    if (rank == 0) {
-      if (threadIdx.x == 0) {
-        const int l = (int)atomicAdd(counter, 1u);
-        s_line = l;
-        st_cluster_s32(line_remote, l);
-      }
+  const int k = int(rank >> 1);
+  const bool chain_cta = (rank & 1u) == 0u;
+  // chain CTA: [nxe] producer sums c_i, then [3][kLpStage][32] push coefficients
+  // (16-byte aligned: cp.async destinations); producer CTA: [2][nxe] copy of
+  // the previous line (k > 0)
+  double* cs = reinterpret_cast<double*>(lp4_smem);
+  double* pbuf = cs + nxe;
+  const unsigned cs_remote = dsmem_addr(cs, rank & ~1u);                 // producer -> its chain's c buffer
+  const unsigned xin_remote = (chain_cta && k + 1 < NL) ? dsmem_addr(cs, unsigned(2 * k + 3)) : 0u;
+  cluster_barrier();   // every CTA running before any distributed shared memory access
+  for (int grp = 0;; ++grp) {
+    __syncthreads();     // this CTA is done with the previous group's buffers
+    const int par = grp & 1;
+    if (rank == 0 && threadIdx.x == 0) {
+      const int g = (int)atomicAdd(counter, 1u);
+      for (unsigned r = 0; r < 2u * NL; ++r) st_cluster_s32(dsmem_addr(&s_group, r), g);
+    }
+    if (chain_cta) {
       for (int t = threadIdx.x; t < nx; t += blockDim.x) reinterpret_cast<unsigned long long*>(cs)[t] = kPending;
+    } else if (k > 0) {
+      for (int t = threadIdx.x; t < nx; t += blockDim.x) reinterpret_cast<unsigned long long*>(cs + par * nxe)[t] = kPending;
     }
     cluster_barrier();
-    const int line = s_line;
-    if (line >= M.nlines) return;
-    if (rank == 1) {
-      lp4_producer<MIRROR, UPDATE, WIN, LPR>(M, b, x, u, cs_remote, line, warp, lane, err);
+    const int g = s_group;
+    if (g * NL >= M.nlines) return;
+    const int line = g * NL + k;
+    if (line >= M.nlines) continue;   // the last group may be partial
+    if (!chain_cta) {
+      lp4_producer<MIRROR, UPDATE, WIN, LPR>(M, b, x, u, cs_remote, k > 0 ? cs + par * nxe : nullptr, line, warp,
+                                             lane, err);
       continue;
     }
     if (warp != 0) continue;
-    // ----------------------------- chain (rank 0) -----------------------------
+    // ----------------------------- chain ------------------------------------
     const int row0 = line * nx;
+    const bool push_next = xin_remote != 0u && line + 1 < M.nlines;
+    const unsigned xin_next = xin_remote + 8u * unsigned(par * nxe);
     lp_stage_push(pbuf, M.push, row0, 0, nx, lane);
     cp_async_commit();
     lp_stage_push(pbuf + kLpStage * 32, M.push, row0, kLpStage, nx, lane);
@@ -768,7 +825,7 @@ __global__ void __launch_bounds__(32 * kLp4Warps, 1)
         if (ix < nx) {
           const int s = ix & 31;
           const double xi = __shfl_sync(0xffffffffu, acc, s);
-          acc = (lane == s) ? 0.0 : fma(-cf[q], xi, acc);
+          acc = keep_if(lane != s, fma(-cf[q], xi, acc));
           if ((q % G) == G - 1) {   // ix0 is a multiple of kLpStage, so this is (ix % G) == G - 1
             // c of rows [ix + 1 + A, ix + 1 + A + G) enters their lanes
             const int ia0 = ix + 1 + A;
@@ -777,9 +834,9 @@ __global__ void __launch_bounds__(32 * kLp4Warps, 1)
           }
           if (lane == 0) {
             // a NaN must never read as the pending marker
-            const double xo = (unsigned long long)__double_as_longlong(xi) == kPending
-                                  ? __longlong_as_double(0x7FF8000000000000ll) : xi;
-            st_relaxed_f64(x + lp_vec<MIRROR>(row0 + ix, M.n), xo);
+            const unsigned long long xo = publish_bits(xi);
+            st_relaxed_u64(x + lp_vec<MIRROR>(row0 + ix, M.n), xo);
+            if (NL > 1 && push_next) st_cluster_u64(xin_next + 8u * unsigned(ix), xo);
           }
         }
       }
@@ -810,107 +867,134 @@ namespace pmgk {
 // shared memory (value-as-flag, as in the line-pipelined solves).  Each row
 // sees the same values as the sequential sweep; only the order of its four
 // products differs.  The result is written over x (the old values were
-// consumed by the SpMV that formed t).  One CTA, ceil(m / 32) warps; dynamic
-// shared memory (warps - 1) * m doubles.
+// consumed by the SpMV that formed t).
+//
+// The warps sit on different SMs: one thread-block cluster of ceil(nw / wpc)
+// CTAs of wpc warps (wpc = ceil(nw / 8)), the boundary line going to the next
+// warp's CTA by distributed shared memory.  One warp issues at most one FP64
+// instruction per ~64 cycles on GB300 (measured: independent DFMAs of one
+// warp retire one per 64 cycles, four warps on one SM one per 19 cycles), so
+// a step costs at least its four FMAs, ~256 cycles; warps on one SM would
+// also share that SM's FP64 pipe.  Each lane keeps its own line's (t, c) for
+// the next kWavePrefetch steps in registers (lanes read different lines, so
+// there is no coalescing to gain from staging them).  Per step, the products
+// with the two older values of the line below (SW, S) of the next point are
+// formed while the current point waits for its left neighbour, so that the
+// dependent path of a step is two FMAs (W, then SE).
+// Dynamic shared memory: wave_smem_doubles(m) doubles.
 // ---------------------------------------------------------------------------
 constexpr int kWaveMaxLines = 800;
-constexpr int kWavePrefetch = 4;
+constexpr int kWaveMaxClusterCtas = 8;
+constexpr int kWavePrefetch = 15;
+
+// warps per CTA for a wavefront over m lines
+__host__ __device__ inline int wave_wpc(int m) {
+  const int nw = (m + 31) / 32;
+  return (nw + kWaveMaxClusterCtas - 1) / kWaveMaxClusterCtas;
+}
+// the incoming boundary line of each local warp, [wpc][m]
+__host__ __device__ inline size_t wave_smem_doubles(int m) { return size_t(wave_wpc(m)) * size_t(m); }
 
 template <bool MIRROR>
-__global__ void __launch_bounds__(1024, 1) k_gs_wave(int m, const double* __restrict__ coef,
-                                                     const double* __restrict__ t, double* x, unsigned* err) {
+__global__ void __launch_bounds__(32 * ((kWaveMaxLines + 31) / 32 + kWaveMaxClusterCtas - 1) / kWaveMaxClusterCtas, 1)
+    k_gs_wave(int m, const double* __restrict__ coef, const double* __restrict__ t, double* x, unsigned* err) {
   extern __shared__ __align__(16) unsigned char wave_smem[];
-  volatile double* bnd = reinterpret_cast<double*>(wave_smem);   // [warps - 1][m]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* inb_all = reinterpret_cast<double*>(wave_smem);   // [wpc][m] incoming boundary line of each local warp
+  const int lane = threadIdx.x & 31, lw = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int warp = int(cluster_ctarank()) * wpc + lw;
+  const int nw = (m + 31) / 32;
   const int n = m * m;
-  for (int i = threadIdx.x; i < (nw - 1) * m; i += blockDim.x)
-    reinterpret_cast<volatile unsigned long long*>(bnd)[i] = kPending;
-  __syncthreads();
-  const int l = 32 * warp + lane;
-  const bool line_ok = l < m;
-  const int steps = m + 2 * 31;
-  double h1 = 0.0, h2 = 0.0, h3 = 0.0, xl = 0.0, got = 0.0;
-  // rolling prefetch of (t_i, c_SW, c_S, c_SE, c_W) for the next kWavePrefetch steps
-  double pt[kWavePrefetch], pc[kWavePrefetch][4];
-  auto fetch = [&](int s, double& tv, double (&cv)[4]) {
-    const int c = s - 2 * lane;
-    if (line_ok && c >= 0 && c < m) {
-      const int i = l * m + c;
-      tv = __ldg(t + lp_vec<MIRROR>(i, n));
-      const double2 a = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i);
-      const double2 b = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i + 1);
-      cv[0] = a.x; cv[1] = a.y; cv[2] = b.x; cv[3] = b.y;
-    } else {
-      tv = 0.0; cv[0] = cv[1] = cv[2] = cv[3] = 0.0;
-    }
-  };
-#pragma unroll
-  for (int q = 0; q < kWavePrefetch; ++q) fetch(q, pt[q], pc[q]);
-  const long long t0 = clock64();
-  // Lane 0 of warp w > 0 starts with column 0 of the boundary line in its
-  // history (the other lanes receive it from their neighbour's first step).
-  {
-    const bool need = lane == 0 && warp > 0;
-    unsigned long long v = need ? *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m) : 0ull;
-    for (unsigned it = 1; __any_sync(0xffffffffu, need && v == kPending); ++it) {
-      if (need && v == kPending) v = *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m);
-      if ((it & 63u) == 0u) {
-        const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
-        if (__any_sync(0xffffffffu, expired)) {
-          if (need && v == kPending) { atomicOr(err, 1u); v = 0ull; }
-          break;
-        }
+  for (int i = threadIdx.x; i < wpc * m; i += blockDim.x) reinterpret_cast<unsigned long long*>(inb_all)[i] = kPending;
+  cluster_barrier();   // every buffer reset before any warp of the cluster stores into one
+  if (warp < nw) {
+    const double* inb = inb_all + lw * m;
+    const bool has_prev = warp > 0, has_next = warp + 1 < nw;
+    const unsigned next_addr = has_next ? dsmem_addr(inb_all + ((warp + 1) % wpc) * m, unsigned((warp + 1) / wpc)) : 0u;
+    const int l = 32 * warp + lane;
+    const bool line_ok = l < m;
+    const int steps = m + 2 * 31;
+    const long long t0 = clock64();
+    // rolling prefetch of (t_i, c_SW, c_S, c_SE, c_W) for steps s .. s + kWavePrefetch (registers)
+    double pt[kWavePrefetch + 1], pc[kWavePrefetch + 1][4];
+    auto fetch = [&](int s, double& tv, double (&cv)[4]) {
+      const int c = s - 2 * lane;
+      if (line_ok && c >= 0 && c < m) {
+        const int i = l * m + c;
+        tv = __ldg(t + lp_vec<MIRROR>(i, n));
+        const double2 a = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i);
+        const double2 b = __ldg(reinterpret_cast<const double2*>(coef) + 2 * (size_t)i + 1);
+        cv[0] = a.x; cv[1] = a.y; cv[2] = b.x; cv[3] = b.y;
+      } else {
+        tv = 0.0; cv[0] = cv[1] = cv[2] = cv[3] = 0.0;
       }
-    }
-    if (need) h1 = __longlong_as_double((long long)v);
-  }
-  for (int s0 = 0; s0 < steps; s0 += kWavePrefetch) {
+    };
 #pragma unroll
-    for (int q = 0; q < kWavePrefetch; ++q) {
-      const int s = s0 + q;
-      if (s < steps) {
-        const int c = s - 2 * lane;
-        // line below at column c + 1: lane k - 1's previous output, or for
-        // lane 0 the previous warp's boundary line (warp-uniform wait)
-        double below = got;
-        const bool need = lane == 0 && warp > 0 && c + 1 >= 0 && c + 1 < m;
-        if (lane == 0) below = 0.0;
-        if (__any_sync(0xffffffffu, need)) {
-          unsigned long long v = need ? *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m + c + 1) : 0ull;
-          for (unsigned it = 1; __any_sync(0xffffffffu, need && v == kPending); ++it) {
-            if (need && v == kPending) v = *reinterpret_cast<const volatile unsigned long long*>(bnd + (warp - 1) * m + c + 1);
-            if ((it & 63u) == 0u) {
-              const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
-              if (__any_sync(0xffffffffu, expired)) {
-                if (need && v == kPending) { atomicOr(err, 1u); v = 0ull; }
-                break;
-              }
-            }
+    for (int q = 0; q <= kWavePrefetch; ++q) fetch(q, pt[q], pc[q]);
+    // Bounded warp-uniform wait for lane 0's boundary value at column `col`
+    // (raw: the value read so far).  Other lanes pass through.
+    auto boundary = [&](bool need, int col, unsigned long long raw) -> unsigned long long {
+      for (unsigned it = 1; __any_sync(0xffffffffu, need && raw == kPending); ++it) {
+        if (need && raw == kPending) raw = ld_cluster_local_u64(inb + col);
+        if ((it & 63u) == 0u) {
+          const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+          if (__any_sync(0xffffffffu, expired)) {
+            if (need && raw == kPending) { atomicOr(err, 1u); raw = 0ull; }
+            break;
           }
-          if (need) below = __longlong_as_double((long long)v);
         }
-        h3 = h2;
-        h2 = h1;
-        h1 = below;
-        const bool active = line_ok && c >= 0 && c < m;
-        double out = 0.0;
-        if (active) {
-          out = pt[q];
-          out = fma(-pc[q][0], h3, out);
-          out = fma(-pc[q][1], h2, out);
-          out = fma(-pc[q][2], h1, out);
-          out = fma(-pc[q][3], xl, out);
-          // a NaN must never read as the pending marker
-          if ((unsigned long long)__double_as_longlong(out) == kPending) out = __longlong_as_double(0x7FF8000000000000ll);
-          x[lp_vec<MIRROR>(l * m + c, n)] = out;
-          if (lane == 31 && warp + 1 < nw) bnd[warp * m + c] = out;
+      }
+      return raw;
+    };
+    // below(s): the line below at column c + 1 for step s; bm1 = below(s - 1),
+    // bm2 = below(s - 2).  Lane 0 of warp w > 0 starts with column 0 of the
+    // boundary line as below(-1).
+    double bm1 = 0.0, bm2 = 0.0;
+    {
+      const bool need = lane == 0 && has_prev;
+      const unsigned long long v = boundary(need, 0, need ? ld_cluster_local_u64(inb) : 0ull);
+      if (need) bm1 = __longlong_as_double((long long)v);
+    }
+    // lane 0's boundary value for the next step, read one step ahead
+    unsigned long long nb = (lane == 0 && has_prev && 1 < m) ? ld_cluster_local_u64(inb + 1) : 0ull;
+    double xl = 0.0, got = 0.0;
+    double part = fma(-pc[0][1], bm1, fma(-pc[0][0], bm2, pt[0]));   // step 0: t - c_SW below(-2) - c_S below(-1)
+    for (int s0 = 0; s0 < steps; s0 += kWavePrefetch + 1) {
+#pragma unroll
+      for (int q = 0; q <= kWavePrefetch; ++q) {
+        const int s = s0 + q;
+        if (s < steps) {
+          constexpr int R = kWavePrefetch + 1;
+          const int qn = (q + 1) % R;   // slot of step s + 1
+          const int c = s - 2 * lane;
+          double bs = lane == 0 ? 0.0 : got;
+          const bool need = lane == 0 && has_prev && s + 1 < m;
+          if (__any_sync(0xffffffffu, need)) {
+            const unsigned long long v = boundary(need, s + 1, nb);
+            if (need) bs = __longlong_as_double((long long)v);
+            if (lane == 0 && s + 2 < m) nb = ld_cluster_local_u64(inb + s + 2);
+          }
+          // dependent path: W (left neighbour, out(s - 1)), then SE (below(s))
+          const double o1 = fma(-pc[q][3], xl, part);
+          const double pn1 = fma(-pc[qn][0], bm1, pt[qn]);       // next point: t - c_SW below(s - 1)
+          double out = fma(-pc[q][2], bs, o1);
+          part = fma(-pc[qn][1], bs, pn1);                        //             - c_S below(s)
+          const bool active = line_ok && c >= 0 && c < m;
+          out = active ? out : 0.0;
+          got = __shfl_up_sync(0xffffffffu, out, 1);
+          if (active) {
+            x[lp_vec<MIRROR>(l * m + c, n)] = out;
+            // a NaN must never read as the pending marker
+            if (lane == 31 && has_next) st_cluster_u64(next_addr + 8u * unsigned(c), publish_bits(out));
+          }
+          xl = out;
+          bm2 = bm1;
+          bm1 = bs;
+          fetch(s + R, pt[q], pc[q]);
         }
-        xl = out;
-        got = __shfl_up_sync(0xffffffffu, out, 1);
-        fetch(s + kWavePrefetch, pt[q], pc[q]);
       }
     }
   }
+  cluster_barrier();   // no CTA leaves while a peer may still store into its shared memory
 }
 
 }  // namespace pmgk

@@ -171,10 +171,11 @@ enum : unsigned char { kVarLp2 = 0, kVarRing = 1, kVarLines = 2, kVarCluster = 3
 // single-vector sweeps of 2D P1 levels: value 2 selects the wavefront kernel
 constexpr unsigned char kVarWave = kVarLines;
 // Chain configurations of the clustered kernel k_lp4: producer sums enter the
-// chain in groups of G rows, A+1 .. A+G rows ahead.
-struct Lp4Cfg { int G, A; };
-constexpr Lp4Cfg kLp4Cfgs[] = {{1, 1}, {2, 1}, {4, 1}, {8, 1}};
-constexpr int kNumLp4Cfgs = 4;
+// chain in groups of G rows, A+1 .. A+G rows ahead; a cluster takes NL
+// consecutive lines at a time.
+struct Lp4Cfg { int G, A, NL; };
+constexpr Lp4Cfg kLp4Cfgs[] = {{1, 1, 1}, {2, 1, 1}, {4, 1, 1}, {8, 1, 1}, {2, 1, 2}, {4, 1, 2}, {2, 1, 4}, {4, 1, 4}};
+constexpr int kNumLp4Cfgs = 8;
 struct PTune {
   unsigned char sL = kVarCluster, sU = kVarCluster;   // single vector: forward / backward ILUT solve
   unsigned char cL = 1, cU = 1;                       // k_lp4 chain configuration (index into kLp4Cfgs)
@@ -511,40 +512,44 @@ bool lp_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double*
 }
 
 // Chain/producer split over two-CTA clusters (k_lp4), chain configuration G, A.
-template <bool MIR, bool UPD, int WIN, int LPR, int G, int A>
+template <bool MIR, bool UPD, int WIN, int LPR, int G, int A, int NL>
 bool lp4_launch_t(Ctx& c, const pmgk::Lp2& M, const double* b, double* x, double* u) {
-  const size_t smem = (size_t((M.nx + 1) & ~1) + size_t(3) * pmgk::kLpStage * 32) * sizeof(double);
+  const size_t smem = size_t(pmgk::lp4_smem_doubles_for(M.nx)) * sizeof(double);
   if (smem > kLpSmemCap) return false;
-  const void* fn = (const void*)pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A>;
+  const void* fn = (const void*)pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A, NL>;
   allow_smem(fn);
-  const int clusters = std::max(1, std::min(M.nlines, c.h->sms / 2));
+  const int clusters = std::max(1, std::min((M.nlines + NL - 1) / NL, c.h->sms / (2 * NL)));
   unsigned* cnt = next_counter(c);
   // the output starts as "pending" (all-ones bytes); rows publish by overwriting it
   c.w->note(cudaMemsetAsync(x, 0xFF, size_t(M.n) * sizeof(double), c.s), "pending fill of a solve's output");
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * clusters);
+  cfg.gridDim = dim3(2 * NL * clusters);
   cfg.blockDim = dim3(32 * pmgk::kLp4Warps);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = c.s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.x = 2 * NL;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
   pmgk::Lp2 m = M;
-  c.w->note(cudaLaunchKernelEx(&cfg, pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A>, m, b, x, u, cnt, c.w->err),
+  c.w->note(cudaLaunchKernelEx(&cfg, pmgk::k_lp4<MIR, UPD, WIN, LPR, G, A, NL>, m, b, x, u, cnt, c.w->err),
             "cluster launch of the line-pipelined solve");
   return true;
 }
 template <bool MIR, bool UPD, int WIN, int LPR>
 bool lp4_launch_c(Ctx& c, int cfg, const pmgk::Lp2& M, const double* b, double* x, double* u) {
   switch (cfg) {
-    case 0: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[0].G, kLp4Cfgs[0].A>(c, M, b, x, u);
-    case 1: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[1].G, kLp4Cfgs[1].A>(c, M, b, x, u);
-    case 2: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[2].G, kLp4Cfgs[2].A>(c, M, b, x, u);
-    case 3: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[3].G, kLp4Cfgs[3].A>(c, M, b, x, u);
+    case 0: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[0].G, kLp4Cfgs[0].A, kLp4Cfgs[0].NL>(c, M, b, x, u);
+    case 1: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[1].G, kLp4Cfgs[1].A, kLp4Cfgs[1].NL>(c, M, b, x, u);
+    case 2: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[2].G, kLp4Cfgs[2].A, kLp4Cfgs[2].NL>(c, M, b, x, u);
+    case 3: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[3].G, kLp4Cfgs[3].A, kLp4Cfgs[3].NL>(c, M, b, x, u);
+    case 4: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[4].G, kLp4Cfgs[4].A, kLp4Cfgs[4].NL>(c, M, b, x, u);
+    case 5: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[5].G, kLp4Cfgs[5].A, kLp4Cfgs[5].NL>(c, M, b, x, u);
+    case 6: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[6].G, kLp4Cfgs[6].A, kLp4Cfgs[6].NL>(c, M, b, x, u);
+    case 7: return lp4_launch_t<MIR, UPD, WIN, LPR, kLp4Cfgs[7].G, kLp4Cfgs[7].A, kLp4Cfgs[7].NL>(c, M, b, x, u);
     default: return false;
   }
 }
@@ -720,19 +725,32 @@ bool wave_sweep(Ctx& c, const DevHLevel& D, bool backward, const double* b, doub
   const double* coef = backward ? D.wave_b : D.wave_f;
   if (!coef) return false;
   const int m = int(std::lround(std::sqrt(double(D.N))));
-  const int warps = (m + 31) / 32;
-  const size_t smem = size_t(warps - 1) * size_t(m) * sizeof(double);
-  if (smem > kLpSmemCap || m * m != D.N) return false;
+  if (m * m != D.N || m > pmgk::kWaveMaxLines) return false;
+  const int wpc = pmgk::wave_wpc(m), nw = (m + 31) / 32, ncta = (nw + wpc - 1) / wpc;
+  const size_t smem = pmgk::wave_smem_doubles(m) * sizeof(double);
+  if (smem > kLpSmemCap) return false;
   double* t = c.w->hr[&D - c.h->dh.data()];
   const double nnz_old = 0.5 * double(D.nnzA - D.N);   // strictly lower / upper part (symmetric pattern)
   launch(c, PMG_K_GS, 12.0 * nnz_old + 4.0 * (D.N + 1) + 32.0 * D.N, [&] {
     spmv<3>(backward ? D.Lo : D.Up, backward ? D.avg_lo : D.avg_up, x, b, t, c.s, c.h->sms, D.dinv);
   });
   launch(c, PMG_K_GS, 48.0 * D.N, [&] {
-    const void* fn = backward ? (const void*)pmgk::k_gs_wave<true> : (const void*)pmgk::k_gs_wave<false>;
-    allow_smem(fn);
-    if (backward) pmgk::k_gs_wave<true><<<1, 32 * warps, smem, c.s>>>(m, coef, t, x, c.w->err);
-    else pmgk::k_gs_wave<false><<<1, 32 * warps, smem, c.s>>>(m, coef, t, x, c.w->err);
+    // one cluster of ncta CTAs (ncta <= 8, the portable cluster size)
+    allow_smem(backward ? (const void*)pmgk::k_gs_wave<true> : (const void*)pmgk::k_gs_wave<false>);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(ncta));
+    cfg.blockDim = dim3(unsigned(32 * wpc));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(ncta);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (backward) c.w->note(cudaLaunchKernelEx(&cfg, pmgk::k_gs_wave<true>, m, coef, (const double*)t, x, c.w->err), "wavefront sweep launch");
+    else c.w->note(cudaLaunchKernelEx(&cfg, pmgk::k_gs_wave<false>, m, coef, (const double*)t, x, c.w->err), "wavefront sweep launch");
   });
   return true;
 }
@@ -1641,11 +1659,11 @@ pmg_status pmg_info(pmg_handle h, pmg_info_t* info) {
   for (size_t l = 0; l < H.lev.size(); ++l) {
     const PTune t = l < h->ptune.size() ? h->ptune[l] : PTune{};
     info->tune_p[l] = t.sL | (t.sU << 2) | (t.bL[0] << 4) | (t.bU[0] << 6) | (t.bL[1] << 8) | (t.bU[1] << 10) |
-                      (t.cL << 12) | (t.cU << 14);
+                      (t.cL << 12) | (t.cU << 15);
   }
   for (size_t j = 0; j < H.hl.size(); ++j) {
     const HTune t = j < h->htune.size() ? h->htune[j] : HTune{};
-    info->tune_h[j] = t.gF | (t.gB << 2) | (t.bF << 4) | (t.bB << 6) | (t.cF << 8) | (t.cB << 10);
+    info->tune_h[j] = t.gF | (t.gB << 2) | (t.bF << 4) | (t.bB << 6) | (t.cF << 8) | (t.cB << 11);
   }
   return PMG_OK;
 }
@@ -2088,13 +2106,13 @@ pmg_status pmg_set_kernels(pmg_handle h, const int* tune_p, const int* tune_h) {
     PTune& t = h->ptune[l];
     t.sL = field(v, 0); t.sU = field(v, 1);
     t.bL[0] = field(v, 2); t.bU[0] = field(v, 3); t.bL[1] = field(v, 4); t.bU[1] = field(v, 5);
-    t.cL = field(v, 6); t.cU = field(v, 7);
+    t.cL = (v >> 12) & 7; t.cU = (v >> 15) & 7;
   }
   for (size_t j = 0; j < h->dh.size(); ++j) {
     const int v = tune_h[j];
     HTune& t = h->htune[j];
     t.gF = field(v, 0); t.gB = field(v, 1); t.bF = field(v, 2); t.bB = field(v, 3);
-    t.cF = field(v, 4); t.cB = field(v, 5);
+    t.cF = (v >> 8) & 7; t.cB = (v >> 11) & 7;
   }
   ++h->tune_epoch;
   return PMG_OK;

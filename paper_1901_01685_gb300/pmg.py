@@ -74,12 +74,12 @@ class pmg_info_t(C.Structure):
             ("single_L", "single_U", "batched64_L", "batched64_U", "batched32_L", "batched32_U"))}
             for v in list(self.tune_p)[:nl]]
         for v, k in zip(list(self.tune_p)[:nl], d["kernels_p"]):
-            k["chain_cfg_L"], k["chain_cfg_U"] = (v >> 12) & 3, (v >> 14) & 3
+            k["chain_cfg_L"], k["chain_cfg_U"] = (v >> 12) & 7, (v >> 15) & 7
         sweep = ("windowed", "ring", "wavefront", "cluster")
         d["kernels_h"] = [{f: (sweep if b < 2 else names)[(v >> (2 * b)) & 3] for b, f in enumerate(
             ("single_fwd", "single_bwd", "batched_fwd", "batched_bwd"))} for v in list(self.tune_h)[:nh]]
         for v, k in zip(list(self.tune_h)[:nh], d["kernels_h"]):
-            k["chain_cfg_fwd"], k["chain_cfg_bwd"] = (v >> 8) & 3, (v >> 10) & 3
+            k["chain_cfg_fwd"], k["chain_cfg_bwd"] = (v >> 8) & 7, (v >> 11) & 7
         return d
 
 
@@ -421,13 +421,13 @@ class Solver:
 
     def set_kernels(self, single=1, batched=1, sweep_single=1, sweep_batched=1, chain_cfg=1):
         """One variant for every level: single-vector solves 0 (windowed), 1
-        (ring) or 3 (chain and producers on a two-CTA cluster, chain
-        configuration chain_cfg 0..3); single-vector sweeps also 2 (wavefront,
+        (ring) or 3 (chain and producers on clusters of two CTAs per line, chain
+        configuration chain_cfg 0..7); single-vector sweeps also 2 (wavefront,
         2D levels); batched solves 1 (ring) or 2 (lines per CTA)."""
         tp = (single | (single << 2) | (batched << 4) | (batched << 6) | (batched << 8) | (batched << 10) |
-              (chain_cfg << 12) | (chain_cfg << 14))
+              (chain_cfg << 12) | (chain_cfg << 15))
         th = (sweep_single | (sweep_single << 2) | (sweep_batched << 4) | (sweep_batched << 6) |
-              (chain_cfg << 8) | (chain_cfg << 10))
+              (chain_cfg << 8) | (chain_cfg << 11))
         pmg_set_kernels(self.h, [tp] * self.info["nlevels"], [th] * self.info["nhlevels"])
         self.info = pmg_info(self.h).as_dict()
 

@@ -78,7 +78,8 @@ CASES = [(0, 3, 5), (1, 2, 5), (2, 2, 3)]
 
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("single,sweep,cfg", [(0, 0, 0), (1, 1, 0), (0, 1, 0), (1, 0, 0),
-                                              (3, 3, 0), (3, 3, 1), (3, 3, 2), (3, 3, 3), (3, 1, 2), (3, 2, 1)])
+                                              (3, 3, 0), (3, 3, 1), (3, 3, 2), (3, 3, 3), (3, 3, 4), (3, 3, 5),
+                                              (3, 3, 6), (3, 3, 7), (3, 1, 2), (3, 2, 6)])
 def test_single_vector_variants_match_oracle(torch_mod, pmg, oracle_mod, case, single, sweep, cfg):
     S, O = _pair(pmg, oracle_mod, *case)
     S.set_kernels(single=single, sweep_single=sweep, chain_cfg=cfg)
