@@ -178,13 +178,13 @@ constexpr Lp4Cfg kLp4Cfgs[] = {{1, 1, 1}, {2, 1, 1}, {4, 1, 1}, {8, 1, 1}, {2, 1
 constexpr int kNumLp4Cfgs = 8;
 struct PTune {
   unsigned char sL = kVarCluster, sU = kVarCluster;   // single vector: forward / backward ILUT solve
-  unsigned char cL = 1, cU = 1;                       // k_lp4 chain configuration (index into kLp4Cfgs)
+  unsigned char cL = 7, cU = 7;                       // k_lp4 chain configuration (index into kLp4Cfgs)
   unsigned char bL[2] = {kVarRing, kVarRing};         // batched, [0] FP64, [1] FP32
   unsigned char bU[2] = {kVarRing, kVarRing};
 };
 struct HTune {
   unsigned char gF = kVarWave, gB = kVarWave;         // single vector: forward / backward sweep
-  unsigned char cF = 1, cB = 1;                       // k_lp4 chain configuration of the sweeps
+  unsigned char cF = 7, cB = 7;                       // k_lp4 chain configuration of the sweeps
   unsigned char bF = kVarRing, bB = kVarRing;         // batched
 };
 

@@ -419,7 +419,7 @@ class Solver:
         self.info = pmg_info(self.h).as_dict()
         return self.info["kernels_p"], self.info["kernels_h"]
 
-    def set_kernels(self, single=1, batched=1, sweep_single=1, sweep_batched=1, chain_cfg=1):
+    def set_kernels(self, single=1, batched=1, sweep_single=1, sweep_batched=1, chain_cfg=7):
         """One variant for every level: single-vector solves 0 (windowed), 1
         (ring) or 3 (chain and producers on clusters of two CTAs per line, chain
         configuration chain_cfg 0..7); single-vector sweeps also 2 (wavefront,
