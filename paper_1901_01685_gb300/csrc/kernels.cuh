@@ -895,6 +895,26 @@ __host__ __device__ inline int wave_wpc(int m) {
 // the incoming boundary line of each local warp, [wpc][m]
 __host__ __device__ inline size_t wave_smem_doubles(int m) { return size_t(wave_wpc(m)) * size_t(m); }
 
+// Lane 0's boundary value at column col of its incoming line (raw: the value
+// read so far): a bounded warp-uniform poll, called only while the value is
+// pending and kept out of line, so that the unrolled step body holds no loop
+// (with the loop inlined in every step a step took ~200 cycles longer, even
+// in warps that never wait).
+__device__ __noinline__ unsigned long long wave_wait_boundary(const double* inb, bool need, int col,
+                                                              unsigned long long raw, long long t0, unsigned* err) {
+  for (unsigned it = 1; __any_sync(0xffffffffu, need && raw == kPending); ++it) {
+    if (need && raw == kPending) raw = ld_cluster_local_u64(inb + col);
+    if ((it & 63u) == 0u) {
+      const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
+      if (__any_sync(0xffffffffu, expired)) {
+        if (need && raw == kPending) { atomicOr(err, 1u); raw = 0ull; }
+        break;
+      }
+    }
+  }
+  return raw;
+}
+
 template <bool MIRROR>
 __global__ void __launch_bounds__(32 * ((kWaveMaxLines + 31) / 32 + kWaveMaxClusterCtas - 1) / kWaveMaxClusterCtas, 1)
     k_gs_wave(int m, const double* __restrict__ coef, const double* __restrict__ t, double* x, unsigned* err) {
@@ -930,19 +950,9 @@ __global__ void __launch_bounds__(32 * ((kWaveMaxLines + 31) / 32 + kWaveMaxClus
     };
 #pragma unroll
     for (int q = 0; q <= kWavePrefetch; ++q) fetch(q, pt[q], pc[q]);
-    // Bounded warp-uniform wait for lane 0's boundary value at column `col`
-    // (raw: the value read so far).  Other lanes pass through.
+    // lane 0's boundary value at column col; other lanes pass through
     auto boundary = [&](bool need, int col, unsigned long long raw) -> unsigned long long {
-      for (unsigned it = 1; __any_sync(0xffffffffu, need && raw == kPending); ++it) {
-        if (need && raw == kPending) raw = ld_cluster_local_u64(inb + col);
-        if ((it & 63u) == 0u) {
-          const bool expired = ld_relaxed(err) != 0u || clock64() - t0 > kWaitCycles;
-          if (__any_sync(0xffffffffu, expired)) {
-            if (need && raw == kPending) { atomicOr(err, 1u); raw = 0ull; }
-            break;
-          }
-        }
-      }
+      if (__any_sync(0xffffffffu, need && raw == kPending)) raw = wave_wait_boundary(inb, need, col, raw, t0, err);
       return raw;
     };
     // below(s): the line below at column c + 1 for step s; bm1 = below(s - 1),
