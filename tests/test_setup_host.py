@@ -129,3 +129,29 @@ def test_calls_reject_null_and_out_of_order_arguments(pmg):
         assert pmg.pmg_last_error() != ""
     finally:
         pmg.pmg_destroy(h)
+
+
+def test_kernel_choice_words_decode(pmg):
+    """pmg_info_t.tune_p / tune_h: 2-bit variant fields, then 3-bit chain
+    configurations (bits 12-14 / 15-17 of tune_p, 8-10 / 11-13 of tune_h).
+    Defaults after setup: clustered single-vector solves with four lines a
+    cluster (configuration 7), wavefront single-vector sweeps, ring kernels
+    for the batched forms."""
+    S = pmg.Solver(0, 3, 5, upload=False)
+    for k in S.info["kernels_p"]:
+        assert (k["single_L"], k["single_U"]) == ("cluster", "cluster")
+        assert (k["chain_cfg_L"], k["chain_cfg_U"]) == (7, 7)
+        assert k["batched64_L"] == k["batched32_U"] == "ring"
+    for k in S.info["kernels_h"]:
+        assert (k["single_fwd"], k["single_bwd"]) == ("wavefront", "wavefront")
+        assert (k["chain_cfg_fwd"], k["chain_cfg_bwd"]) == (7, 7)
+    info = pmg.pmg_info_t()
+    info.nlevels, info.nhlevels = 1, 1
+    info.tune_p[0] = 3 | (1 << 2) | (1 << 4) | (2 << 6) | (1 << 8) | (2 << 10) | (5 << 12) | (6 << 15)
+    info.tune_h[0] = 2 | (3 << 2) | (1 << 4) | (2 << 6) | (4 << 8) | (3 << 11)
+    d = info.as_dict()
+    kp, kh = d["kernels_p"][0], d["kernels_h"][0]
+    assert (kp["single_L"], kp["single_U"], kp["batched64_L"], kp["batched64_U"]) == ("cluster", "ring", "ring", "lines")
+    assert (kp["batched32_L"], kp["batched32_U"], kp["chain_cfg_L"], kp["chain_cfg_U"]) == ("ring", "lines", 5, 6)
+    assert (kh["single_fwd"], kh["single_bwd"], kh["batched_fwd"], kh["batched_bwd"]) == ("wavefront", "cluster", "ring", "lines")
+    assert (kh["chain_cfg_fwd"], kh["chain_cfg_bwd"]) == (4, 3)
