@@ -110,7 +110,7 @@ typedef struct {
   double cycle_bytes;                   /* algorithmic DRAM bytes of one V-cycle */
   double cycle_flops;                   /* floating-point operations of one V-cycle */
   /* kernel variant of each solve (0 windowed line-pipelined, 1 ring, 2 lines
-   * per CTA, 3 chain and producers on a two-CTA cluster), two bits each.
+   * per CTA, 3 chain and producers on clusters of two CTAs a line), two bits each.
    * tune_p[l]: single-vector forward, backward; batched FP64 forward,
    * backward; batched FP32 forward, backward (2 bits each, bits 0-11); then
    * the chain configuration of the clustered kernel for the forward and the
